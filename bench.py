@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Benchmark of the occupancy-grid ray sampler on one GB300 (or N, as
+independent replicas of the per-frame work).
+
+One step = one frame of the object-centric workload (one 128^3 level over
+[-1.5, 1.5)^3, 800x800 rays from one of 20 seeded cameras, step
+fl32(sqrt(3)*3/1024), near 2, far 6): rebuild the VDB grid from the dense
+occupancy, hierarchical-DDA sampling (count, scan, emit), and compositing
+over the 64-blob field.  Rays of all 20 cameras stay resident in HBM; the L2
+is flushed between timed steps (the flush is outside the timed windows).
+
+Prints one JSON line (rank 0).  `value` is rays/s of the whole step; the
+line also carries the sampler alone for HDDA and for the dense-DDA
+baseline (rays/s, samples/s), per-kernel times, the roofline of the
+dominant kernel, the end-to-end rate through the public API with host
+buffers, and the CPU oracle's rate on a bounded sample of the same work.
+
+--impl reference times the CPU oracle (binary32 brute-force sampler plus
+binary64 compositor) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_CAMERAS = 20
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-stride", type=int, default=16,
+                    help="CPU baseline sample: every n-th ray of camera 0")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2404_10272_gb300 import hdda, scenes
+
+    sc = scenes.object_scene()
+    cams = scenes.object_cameras(n=N_CAMERAS)
+    rays = [c.rays() for c in cams]
+    n = rays[0][0].shape[0]
+    O = torch.stack([torch.from_numpy(o) for o, _ in rays]).cuda()
+    D = torch.stack([torch.from_numpy(d) for _, d in rays]).cuda()
+    dense = torch.from_numpy(sc.occ).cuda()
+    field = torch.from_numpy(sc.field).cuda()
+    p = sc.params
+    prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    gv = hdda.build_vdb(dense, sc.aabbs)
+    gd = hdda.pack_dense(dense, sc.aabbs)
+    vstats = gv.stats()
+
+    totals = [hdda.traverse_hdda(O[c], D[c], gv, prm, count_only=True).total
+              for c in range(N_CAMERAS)]
+    cap = max(totals)
+    bufs = hdda.alloc_samples(n, cap)
+    rgba = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def cam_of(j):
+        return (rank * 7 + j) % N_CAMERAS
+
+    def step_hdda(j):
+        c = cam_of(j)
+        gv.rebuild(dense)
+        s = hdda.traverse_hdda(O[c], D[c], gv, prm, out=bufs)
+        hdda.composite(O[c], D[c], s, field, out=rgba)
+        return s.total
+
+    def step_dense(j):
+        c = cam_of(j)
+        gd.rebuild(dense)
+        s = hdda.traverse_dense(O[c], D[c], gd, prm, out=bufs)
+        hdda.composite(O[c], D[c], s, field, out=rgba)
+        return s.total
+
+    def sampler_hdda(j):
+        c = cam_of(j)
+        return hdda.traverse_hdda(O[c], D[c], gv, prm, out=bufs).total
+
+    def sampler_dense(j):
+        c = cam_of(j)
+        return hdda.traverse_dense(O[c], D[c], gd, prm, out=bufs).total
+
+    def timed(fn, steps, warmup, profile=False, clocks=None):
+        for j in range(warmup):
+            fn(j)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        if profile:
+            hdda.profiler_read()
+            hdda.profiler_enable(True)
+        evs = []
+        samples = 0
+        for j in range(steps):
+            flush.zero_()   # evict the previous step's data from L2 (outside the window)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            samples += fn(warmup + j)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        kern = {}
+        if profile:
+            hdda.profiler_enable(False)
+            kern = hdda.profiler_read()
+        clk = clocks.stop() if clocks else None
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, samples, kern, clk
+
+    K, W = args.steps, args.warmup
+    clocks = ClockSampler(local)
+    ms, samples, kern, clk = timed(step_hdda, K, W, profile=True, clocks=clocks)
+    ms_dense, samples_dense, kern_dense, _ = timed(step_dense, max(3, K // 2), 2, profile=True)
+    ms_sh, samp_sh, _, _ = timed(sampler_hdda, K, 2)
+    ms_sd, samp_sd, _, _ = timed(sampler_dense, max(3, K // 2), 2)
+
+    total_rays = n * K * world
+    value = total_rays / (ms / 1e3)
+
+    # --- end to end through the public API with host buffers ---------------
+    e2e = None
+    if world >= 1:
+        o_host = [torch.from_numpy(o).pin_memory() for o, _ in rays[:4]]
+        d_host = [torch.from_numpy(d).pin_memory() for _, d in rays[:4]]
+        out_host = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+        o_dev = torch.empty_like(O[0])
+        d_dev = torch.empty_like(D[0])
+        steps_e2e = max(3, K // 2)
+
+        def e2e_step(j):
+            c = j % 4
+            o_dev.copy_(o_host[c], non_blocking=True)
+            d_dev.copy_(d_host[c], non_blocking=True)
+            gv.rebuild(dense)
+            s = hdda.traverse_hdda(o_dev, d_dev, gv, prm, out=bufs)
+            hdda.composite(o_dev, d_dev, s, field, out=rgba)
+            out_host.copy_(rgba, non_blocking=True)
+            return s.total
+
+        for j in range(2):
+            e2e_step(j)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(steps_e2e):
+            e2e_step(j)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": n * steps_e2e * world / el, "unit": "rays/s",
+               "h2d_bytes_per_step": int(2 * n * 3 * 4),
+               "d2h_bytes_per_step": int(n * 4 * 4 + 16)}
+
+    # --- roofline of the dominant kernel -----------------------------------
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    S_avg = samples / K
+    grid_bytes = int(vstats.bytes)
+    # algorithmic bytes per launch ("Roofline")
+    alg = {
+        "hdda_count": 24 * n + 8 * n + grid_bytes,
+        "hdda_emit": 8 * n + 8 * (n + 1) + 12 * S_avg,
+        "composite": 24 * n + 8 * (n + 1) + 8 * S_avg + 16 * n + 64 * 32,
+        "build_vdb": sc.occ.size + grid_bytes,
+    }
+    per_kernel = {}
+    for name, (launches, tot_ms) in kern.items():
+        avg = tot_ms / max(1, launches)
+        ent = {"launches": launches, "avg_ms": round(avg, 4), "share": round(tot_ms / ms, 4)}
+        if name in alg:
+            ent["alg_bytes"] = int(alg[name])
+            ent["gbs"] = round(alg[name] / (avg / 1e3) / 1e9, 1)
+        per_kernel[name] = ent
+    dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
+    roofline = None
+    if dom is not None:
+        launches, tot_ms = kern[dom]
+        avg = tot_ms / launches
+        ach = alg.get(dom, 0) / (avg / 1e3) / 1e9
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
+                    "peak_source": peak_src}
+    sam_launch = sum(kern.get(k, (1, 0.0))[1] / max(1, kern.get(k, (1, 0.0))[0])
+                     for k in ("hdda_count", "hdda_emit"))
+    sampler_alg = 24 * n + 8 * (n + 1) + 12 * S_avg + grid_bytes
+    roofline_sampler = {"kernels": ["hdda_count", "hdda_emit"], "bound": "hbm",
+                        "achieved": round(sampler_alg / (sam_launch / 1e3) / 1e9, 1),
+                        "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(sampler_alg / (sam_launch / 1e3) / 1e9 / hbm_peak, 4)}
+
+    launches_per_step = sum(v[0] for v in kern.values()) / K if kern else None
+
+    # --- CPU oracle on a bounded sample (rank 0, N = 1) -------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc, rays[0], args.cpu_stride)
+
+    line = {
+        "metric": "rays/sec and samples/sec, HDDA vs dense-DDA on same GB300 (bit-exact); % HBM roofline",
+        "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(ms / K, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "object-centric: 1x128^3 grid over [-1.5,1.5)^3, 800x800 rays, "
+                               "20 cameras on a radius-4 sphere, near 2, far 6, step 0.0050743674, "
+                               "64-blob composite",
+                   "rays_per_step": n, "occupancy": round(sc.info["occupancy"], 4),
+                   "step": "vdb rebuild + hdda count/scan/emit + composite",
+                   "l2": "flushed between steps (256 MiB write), flush outside timed windows",
+                   "parallelism": f"replicas x{world}"},
+        "samples_per_s": round(samples * world / (ms / 1e3), 1),
+        "samples_per_step": int(S_avg),
+        "hdda_sampler": {"rays_per_s": round(n * K * world / (ms_sh / 1e3), 1),
+                         "samples_per_s": round(samp_sh * world / (ms_sh / 1e3), 1),
+                         "ms_per_frame": round(ms_sh / K, 4)},
+        "dense_dda_sampler": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_sd / 1e3), 1),
+                              "samples_per_s": round(samp_sd * world / (ms_sd / 1e3), 1),
+                              "ms_per_frame": round(ms_sd / max(3, K // 2), 4)},
+        "dense_dda_step": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_dense / 1e3), 1),
+                           "ms_per_step": round(ms_dense / max(3, K // 2), 4)},
+        "hdda_vs_dense_sampler_speedup": round(ms_sd / max(3, K // 2) / (ms_sh / K), 3),
+        "grid": {"vdb_bytes": grid_bytes, "dense_bytes": int(vstats.dense_bytes),
+                 "n_leaves": int(vstats.n_leaves), "n_tiles": int(vstats.n_tiles)},
+        "kernels": per_kernel,
+        "kernels_dense_step": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}
+                               for k, v in kern_dense.items()},
+        "roofline": roofline,
+        "roofline_sampler": roofline_sampler,
+        "gpu_launches": int(round(launches_per_step * K)) if launches_per_step else 0,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sc, ray_pair, stride):
+    """Oracle (as it stands) on every stride-th ray of camera 0: sampler + compositor."""
+    import numpy as np
+    import oracle
+
+    o, d = ray_pair
+    sel = np.arange(0, o.shape[0], stride)
+    so, sd = np.ascontiguousarray(o[sel]), np.ascontiguousarray(d[sel])
+    p = sc.params
+    t0 = time.perf_counter()
+    off, idx, a, b = oracle.sample(so, sd, sc.occ, sc.aabbs, p.near, p.far, p.step, p.cone,
+                                   p.max_step, p.max_steps)
+    t1 = time.perf_counter()
+    oracle.composite(so, sd, off, a, b, sc.field)
+    t2 = time.perf_counter()
+    return {"value": round(sel.size / (t2 - t0), 1), "unit": "rays/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"every {stride}th ray of camera 0 ({sel.size} rays, {int(off[-1])} samples)",
+            "sampler_rays_per_s": round(sel.size / (t1 - t0), 1), "seconds": round(t2 - t0, 2)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on bounded samples of the same workload
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2404_10272_gb300 import scenes
+
+    oracle.build()
+    sc = scenes.object_scene()
+    cams = scenes.object_cameras(n=N_CAMERAS)
+    stride = 256  # each step: every 256th ray of one camera (2500 rays)
+
+    def step(j):
+        o, d = cams[j % N_CAMERAS].rays()
+        sel = np.arange(j % stride, o.shape[0], stride)
+        so, sd = np.ascontiguousarray(o[sel]), np.ascontiguousarray(d[sel])
+        p = sc.params
+        t0 = time.perf_counter()
+        off, idx, a, b = oracle.sample(so, sd, sc.occ, sc.aabbs, p.near, p.far, p.step, p.cone,
+                                       p.max_step, p.max_steps)
+        oracle.composite(so, sd, off, a, b, sc.field)
+        return sel.size, time.perf_counter() - t0
+
+    for j in range(args.warmup):
+        step(j)
+    rays = 0
+    el = 0.0
+    for j in range(args.steps):
+        r, t = step(args.warmup + j)
+        rays += r
+        el += t
+    v = rays / el
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "rays/sec and samples/sec, HDDA vs dense-DDA on same GB300 (bit-exact); % HBM roofline",
+        "value": round(v, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "object-centric: 1x128^3 grid, 800x800 rays, 20 cameras, "
+                               "64-blob composite", "parallelism": "cpu, 1 thread"},
+        "cpu_baseline": {"value": round(v, 1), "unit": "rays/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: every {stride}th ray of one camera"},
+        "e2e": {"value": round(v, 1), "unit": "rays/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * hdda.h -- C ABI of libhdda, a GB300 (sm_103a) occupancy-grid ray sampler
+ * with VDB-style sparse grids and hierarchical DDA.
+ *
+ * Method: Kato & Tarashima, "Plug-and-Play Acceleration of Occupancy
+ * Grid-based NeRF Rendering using VDB Grid and Hierarchical Ray Traversal"
+ * (CVPR-W 2024).  A trained dense binary occupancy grid, one level or a
+ * cascade of levels whose voxel size doubles (Sec. 4.1), is rebuilt into a
+ * sparse tree whose uniform blocks become tiles (Sec. 3), and every camera
+ * ray is walked with hierarchical DDA, which skips a whole empty node in one
+ * step (Sec. 2.3, Fig. 1), keeping the lattice samples that fall in occupied
+ * voxels (Algorithm 1).  The dense-grid DDA walk it replaces is exported
+ * beside it.
+ *
+ * Conventions for every call
+ *   - Pointers are DEVICE pointers owned by the caller unless a parameter
+ *     says "host".  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are stream-ordered and return before the GPU work finishes, except
+ *     where a host value is returned (noted per call): those synchronise the
+ *     stream once.
+ *   - Every call returns an hdda_status; 0 is success.  On failure
+ *     hdda_last_error() gives a message (thread-local).  No C++ exception
+ *     crosses this boundary.  A failed call leaves outputs unspecified.
+ *   - Grids are read-only while any traversal that uses them is in flight.
+ *
+ * Grid layout conventions
+ *   - Dense occupancy input: uint8 [levels][res][res][res], C order
+ *     (x slowest, z fastest), non-zero = occupied.  Level 0 is the finest.
+ *   - Level boxes are half-open [lo, hi) per axis.  A point belongs to the
+ *     finest level whose box holds it (Sec. 3, last paragraph).
+ *   - Voxel index of a point x at level l, per axis c, in binary32 with no
+ *     fused multiply-add:
+ *         s_c = res / (hi_c - lo_c)
+ *         i_c = clamp(floor((x_c - lo_c) * s_c), 0, res - 1)
+ */
+#ifndef HDDA_H
+#define HDDA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so the ABI needs no CUDA header. */
+typedef struct CUstream_st* hdda_stream_t;
+
+typedef enum {
+    HDDA_OK = 0,
+    HDDA_ERR_INVALID_ARG = 1, /* bad pointer, size, shape or parameter      */
+    HDDA_ERR_CUDA = 2,        /* a CUDA runtime call failed                 */
+    HDDA_ERR_CAPACITY = 3,    /* output buffer smaller than the sample count */
+    HDDA_ERR_STEP_LIMIT = 4,  /* lattice longer than params.max_steps       */
+    HDDA_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up         */
+    HDDA_ERR_OOM = 6,         /* device allocation failed                   */
+    HDDA_ERR_INTERNAL = 7     /* a device-side consistency check failed     */
+} hdda_status;
+
+#define HDDA_MAX_LEVELS 8
+#define HDDA_MAX_RES 1024
+
+/* Half-open box [lo, hi) of one cascade level, in world units. */
+typedef struct {
+    float lo[3];
+    float hi[3];
+} hdda_aabb;
+
+/*
+ * Lattice parameters shared by every ray of a call (Sec. 3: constant step
+ * for bounded scenes, linearly increasing step for unbounded ones;
+ * Algorithm 1: the lattice advances independently of voxel boundaries).
+ * In binary32, no fused multiply-add:
+ *     t_0 = near_t
+ *     t_{k+1} = t_k + min(max(t_k * cone_angle, step), max_step)
+ *     candidate k exists iff t_{k+1} <= far_t
+ * All values finite; step > 0, max_step > 0, cone_angle >= 0,
+ * 0 <= max_steps <= 2^24.  More candidates than max_steps is
+ * HDDA_ERR_STEP_LIMIT.  Directions need not be unit length: t is in units
+ * of |d|.
+ */
+typedef struct {
+    float near_t;
+    float far_t;
+    float step;
+    float cone_angle;
+    float max_step;
+    int32_t max_steps;
+} hdda_params;
+
+typedef struct hdda_grid hdda_grid; /* opaque, library-owned device object */
+
+typedef enum { HDDA_GRID_DENSE = 0, HDDA_GRID_VDB = 1 } hdda_grid_kind;
+
+typedef struct {
+    int32_t kind;        /* hdda_grid_kind                                  */
+    int32_t levels;
+    int32_t res;
+    int32_t blocks;      /* ceil(res / 8): 8^3-voxel blocks per axis        */
+    int32_t nodes;       /* ceil(blocks / 16): 16^3-block nodes per axis    */
+    int32_t reserved;
+    int64_t n_leaves;    /* VDB: stored 8^3 leaf bitmasks (partial blocks)  */
+    int64_t n_tiles;     /* VDB: fully occupied blocks stored as tile bits  */
+    int64_t bytes;       /* bytes the traversal reads: level table,
+                            index thresholds, masks and leaves (Table 3)    */
+    int64_t dense_bytes; /* levels * ceil(res^3 / 32) * 4: the dense bit
+                            array the paper starts from (Table 3 caption)   */
+} hdda_grid_stats;
+
+/* Arrays of a grid that hdda_grid_copy_array can export. */
+typedef enum {
+    /* float [levels][3][res+1]: X[a] = smallest binary32 x in [lo, hi] whose
+       voxel index (formula above) is >= a; X[0] = lo, X[res] = hi.  Voxel a
+       along axis c is exactly [X[a], X[a+1]).                               */
+    HDDA_ARRAY_THRESHOLDS = 0,
+    /* uint32 [levels][ceil(res^3/32)]: voxel (x, y, z) of level l is bit
+       ((x*res + y)*res + z) of level l's bit string, bit b of word w being
+       voxel 32w + b (DENSE grids).                                          */
+    HDDA_ARRAY_DENSE_BITS = 1,
+    /* uint32 [levels][nodes^3][128]: 4096-bit child mask per node; block
+       (bx, by, bz) is cell ((bx%16)*16 + by%16)*16 + bz%16 of node
+       ((bx/16)*nodes + by/16)*nodes + bz/16; a bit is set when the block is
+       partly occupied (VDB grids).                                          */
+    HDDA_ARRAY_CHILD_MASK = 2,
+    /* uint32 [levels][nodes^3][128]: tile mask, set when all 512 voxels of
+       the block exist and are occupied (VDB grids).                          */
+    HDDA_ARRAY_TILE_MASK = 3,
+    /* uint32 [levels][nodes^3][128]: global index of the first leaf whose
+       cell lies in each child-mask word (VDB grids).                         */
+    HDDA_ARRAY_LEAF_PREFIX = 4,
+    /* uint32 [n_leaves][16]: 512-bit leaf masks in (level, node, cell)
+       order; voxel (x%8, y%8, z%8) is bit ((x%8)*8 + y%8)*8 + z%8 (VDB).    */
+    HDDA_ARRAY_LEAVES = 5
+} hdda_array;
+
+/* Version string of the library. */
+const char* hdda_version(void);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* hdda_last_error(void);
+
+/*
+ * Dense grid for the dense-DDA baseline: packs `dense` into the bit array
+ * the paper starts from (Sec. 2.2: the occupancy grid is a dense binary grid;
+ * Table 3: 128^3 grid = 256 KiB) and builds the per-axis index thresholds.
+ *   dense   device uint8 [levels][res][res][res]
+ *   levels  1..HDDA_MAX_LEVELS;  res 1..HDDA_MAX_RES
+ *   aabbs   HOST array of `levels` boxes, finite, lo < hi per axis
+ *   out     receives a new grid; free it with hdda_grid_free
+ * Stream-ordered; `dense` may be reused once the stream has passed the call.
+ */
+int hdda_pack_dense(const uint8_t* dense, int levels, int res, const hdda_aabb* aabbs,
+                    hdda_grid** out, hdda_stream_t stream);
+
+/*
+ * VDB-style sparse grid for hierarchical DDA (Sec. 3: the dense grid becomes
+ * a VDB tree; blocks that hold one value become tiles).  Per level: 8^3 leaf
+ * bitmasks for partly occupied blocks, and per 16^3-block node a child mask,
+ * a tile mask and a leaf-index prefix table.  Arguments as hdda_pack_dense;
+ * bytes_out (HOST, may be NULL) receives hdda_grid_stats.bytes, which makes
+ * the call synchronise the stream once.
+ */
+int hdda_build_vdb(const uint8_t* dense, int levels, int res, const hdda_aabb* aabbs,
+                   hdda_grid** out, size_t* bytes_out, hdda_stream_t stream);
+
+/*
+ * Rebuilds a grid in place from new occupancy of the same shape (levels,
+ * res and boxes unchanged), e.g. after an occupancy update during training.
+ * Allocates nothing and does not synchronise; traversals queued on other
+ * streams must not overlap it.
+ */
+int hdda_grid_rebuild(hdda_grid* grid, const uint8_t* dense, hdda_stream_t stream);
+
+/* Fills *out (HOST).  Synchronises the grid's last build stream. */
+int hdda_grid_stats_get(const hdda_grid* grid, hdda_grid_stats* out);
+
+/*
+ * Copies one exported array (see hdda_array) into HOST memory `dst` of
+ * `bytes` bytes; *needed (HOST, may be NULL) receives its size.  With
+ * dst == NULL only the size is returned.  Synchronous.  An array the grid's
+ * kind does not hold is HDDA_ERR_INVALID_ARG.
+ */
+int hdda_grid_copy_array(const hdda_grid* grid, int which, void* dst, size_t bytes,
+                         size_t* needed);
+
+/* Frees a grid (waits for the device to finish with it).  NULL is a no-op. */
+void hdda_grid_free(hdda_grid* grid);
+
+/*
+ * Dense-grid DDA sampler (the baseline the paper replaces; Algorithm 1 with
+ * DDA as the analyzer).  Each ray walks the voxels of the dense bit array
+ * that its lattice visits, one lookup per voxel, and keeps every lattice
+ * interval whose midpoint voxel is occupied at the finest level holding it.
+ *   rays_o, rays_d  device float [n_rays][3]; a ray with a non-finite
+ *                   component has no samples
+ *   grid            a HDDA_GRID_DENSE grid
+ *   params          HOST pointer
+ *   offsets         device int64 [n_rays + 1]: receives CSR row pointers
+ *                   (offsets[r]..offsets[r+1] are ray r's samples)
+ *   ray_idx, t0, t1 device int32 / float / float [capacity]: the kept
+ *                   intervals (r, t_k, t_{k+1}), rays in order, each ray's
+ *                   intervals in ascending k
+ *   capacity        0 = count only: offsets and *total_out are filled and
+ *                   nothing else is written.  Otherwise, if capacity < total
+ *                   the call returns HDDA_ERR_CAPACITY and writes no sample.
+ *   total_out       HOST int64: number of kept intervals
+ * Synchronises the stream once (after counting, to read the total); the
+ * emission that follows is left in flight on the stream.
+ */
+int hdda_traverse_dense(const float* rays_o, const float* rays_d, int64_t n_rays,
+                        const hdda_grid* grid, const hdda_params* params, int64_t* offsets,
+                        int32_t* ray_idx, float* t0, float* t1, int64_t capacity,
+                        int64_t* total_out, hdda_stream_t stream);
+
+/*
+ * Hierarchical-DDA sampler over a VDB grid (Sec. 2.3 and Sec. 3; Algorithm 1
+ * with HDDA as the analyzer).  Arguments and outputs as hdda_traverse_dense;
+ * `grid` must be a HDDA_GRID_VDB grid built from the same occupancy.  Empty
+ * nodes, empty blocks, tiles and single voxels are each crossed in one step;
+ * the result is bit-identical to hdda_traverse_dense.
+ */
+int hdda_traverse_hdda(const float* rays_o, const float* rays_d, int64_t n_rays,
+                       const hdda_grid* grid, const hdda_params* params, int64_t* offsets,
+                       int32_t* ray_idx, float* t0, float* t1, int64_t capacity,
+                       int64_t* total_out, hdda_stream_t stream);
+
+/*
+ * Front-to-back compositing of the kept intervals over a Gaussian-blob field
+ * (Sec. 1: densities and colours of the sampled points are accumulated into
+ * the pixel).  For each ray, in order of its samples, with x the position at
+ * the interval midpoint:
+ *     sigma = sum_g a_g exp(-|x - mu_g|^2 / (2 s_g^2))
+ *     c     = sum_g a_g exp(...) rgb_g / sigma      (0 when sigma == 0)
+ *     alpha = 1 - exp(-sigma (t1 - t0)) ;  C += T alpha c ;  T *= 1 - alpha
+ * and rgba_out[r] = (C, 1 - T): black background, no early termination.
+ *   rays_o, rays_d  device float [n_rays][3]
+ *   offsets         device int64 [n_rays + 1] (as written by a traversal)
+ *   t0, t1          device float samples
+ *   field           device float [n_gauss][8] = mu_x, mu_y, mu_z, s, a, r, g, b
+ *   n_gauss         0..256
+ *   rgba_out        device float [n_rays][4]
+ * Stream-ordered, no synchronisation.
+ */
+int hdda_composite(const float* rays_o, const float* rays_d, int64_t n_rays,
+                   const int64_t* offsets, const float* t0, const float* t1,
+                   const float* field, int n_gauss, float* rgba_out, hdda_stream_t stream);
+
+/*
+ * Kernel timing for measurement.  While enabled, every kernel the library
+ * launches is bracketed by two CUDA events recorded on the stream it is
+ * launched on.  hdda_profiler_read synchronises on those events, writes up
+ * to `cap` per-kernel aggregates (HOST array) and clears them; *n_out
+ * (HOST) receives how many kernels were seen.  Adds one event pair per
+ * launch; meant for benchmarks, off by default.  The paper has no
+ * counterpart (it reports frame rates only).
+ */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} hdda_kernel_time;
+
+int hdda_profiler_enable(int on);
+int hdda_profiler_read(hdda_kernel_time* out, int cap, int* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDDA_H */

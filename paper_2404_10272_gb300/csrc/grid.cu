@@ -1,0 +1,460 @@
+// grid.cu -- dense bit-array packing (the paper's baseline grid) and the
+// GPU builder of the VDB-style sparse grid (Sec. 3: the dense occupancy grid
+// becomes a VDB tree whose uniform blocks are pruned into tiles).
+//
+// Kernels
+//   thresholds_kernel   exact per-axis voxel boundaries X[a] (one thread per
+//                       boundary, binary search over binary32 keys)
+//   pack_dense_kernel   uint8 voxels -> uint32 bit words, one ballot per word
+//   vdb_blocks_kernel   one warp per 8^3 block: 16 ballots give the 512-bit
+//                       leaf mask and the block's empty/partial/full state
+//   vdb_nodes_kernel    one 128-thread CTA per 16^3-block node: ballots over
+//                       the block states give the child and tile masks, a
+//                       CTA scan gives each mask word's leaf-count prefix
+//   vdb_finalize_kernel one CTA: scan of leaf counts over all nodes, global
+//                       leaf prefix per mask word, leaf and tile totals
+//   vdb_scatter_kernel  16 threads per partial block copy its mask into the
+//                       compact leaf pool
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "grid.cuh"
+
+namespace hdda {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__global__ void thresholds_kernel(GridDev g, float* __restrict__ thr) {
+  const int64_t R1 = g.R + 1;
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)g.L * 3 * R1) return;
+  const int a = (int)(idx % R1);
+  const int lc = (int)(idx / R1);
+  const int c = lc % 3, l = lc / 3;
+  const float lo = g.lv[l].lo[c], hi = g.lv[l].hi[c], s = g.lv[l].s[c];
+  float X;
+  if (a == 0) {
+    X = lo;
+  } else if (a == g.R) {
+    X = hi;
+  } else if (voxel_index(hi, lo, s, g.R) < a) {
+    X = hi;  // no point of the box reaches index a
+  } else {
+    // voxel_index is monotone in x, so the set {x : index >= a} is an upper
+    // range of binary32 values; find its first element.
+    uint32_t kl = float_key(lo);  // index(lo) = 0 < a
+    uint32_t kh = float_key(hi);  // index(hi) >= a
+    while (kh - kl > 1u) {
+      uint32_t km = kl + (kh - kl) / 2u;
+      if (voxel_index(key_float(km), lo, s, g.R) >= a) kh = km; else kl = km;
+    }
+    X = key_float(kh);
+  }
+  thr[idx] = X;
+}
+
+__global__ void pack_dense_kernel(const uint8_t* __restrict__ dense, int L, int R, int W,
+                                  uint32_t* __restrict__ bits) {
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t total = (int64_t)L * W;
+  const int64_t w0 = warp * 32;
+  if (w0 >= total) return;  // uniform per warp
+  const int64_t R3 = (int64_t)R * R * R;
+  uint32_t mine = 0;
+  for (int j = 0; j < 32; ++j) {
+    const int64_t gw = w0 + j;
+    bool on = false;
+    if (gw < total) {
+      const int64_t l = gw / W, w = gw % W;
+      const int64_t lin = w * 32 + lane;
+      if (lin < R3) on = dense[l * R3 + lin] != 0;
+    }
+    const uint32_t b = __ballot_sync(kFull, on);
+    if (lane == j) mine = b;
+  }
+  if (w0 + lane < total) bits[w0 + lane] = mine;
+}
+
+__global__ void vdb_blocks_kernel(const uint8_t* __restrict__ dense, int L, int R, int B,
+                                  uint32_t* __restrict__ blk_masks,
+                                  uint8_t* __restrict__ blk_state) {
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t B3 = (int64_t)B * B * B;
+  if (warp >= (int64_t)L * B3) return;  // uniform per warp
+  const int l = (int)(warp / B3);
+  const int64_t b = warp % B3;
+  const int bx = (int)(b / ((int64_t)B * B)), by = (int)((b / B) % B), bz = (int)(b % B);
+  const uint8_t* lvl = dense + (int64_t)l * R * R * R;
+  uint32_t mine = 0;
+  for (int w = 0; w < 16; ++w) {
+    const int v = w * 32 + lane;  // local voxel ((x%8)*8 + y%8)*8 + z%8
+    const int x = bx * 8 + (v >> 6), y = by * 8 + ((v >> 3) & 7), z = bz * 8 + (v & 7);
+    bool on = false;
+    if (x < R && y < R && z < R) on = lvl[((int64_t)x * R + y) * R + z] != 0;
+    const uint32_t bal = __ballot_sync(kFull, on);
+    if (lane == w) mine = bal;
+  }
+  const bool any = __any_sync(kFull, lane < 16 && mine != 0u);
+  const bool all = __all_sync(kFull, lane >= 16 || mine == kFull);
+  if (lane < 16) blk_masks[warp * 16 + lane] = mine;
+  if (lane == 0) blk_state[warp] = all ? kBlockFull : (any ? kBlockPartial : kBlockEmpty);
+}
+
+// Exclusive CTA-wide scan of one uint32 per thread (blockDim.x <= 1024, multiple of 32).
+__device__ uint32_t cta_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t* total_out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < nw ? warp_tot[lane] : 0u;
+    uint32_t ti = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(kFull, ti, o);
+      if (lane >= o) ti += y;
+    }
+    if (lane < nw) warp_tot[lane] = ti - t;  // exclusive warp offsets
+    if (lane == 31) warp_tot[32] = ti;       // CTA total
+  }
+  __syncthreads();
+  uint32_t r = warp_tot[warp] + inc - v;
+  if (total_out) *total_out = warp_tot[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void vdb_nodes_kernel(int L, int B, int N, const uint8_t* __restrict__ blk_state,
+                                 uint32_t* __restrict__ child, uint32_t* __restrict__ tile,
+                                 uint32_t* __restrict__ local_prefix,
+                                 uint32_t* __restrict__ node_leaves,
+                                 uint32_t* __restrict__ node_tiles,
+                                 uint32_t* __restrict__ nstate) {
+  __shared__ uint32_t warp_tot[33];
+  const int64_t N3 = (int64_t)N * N * N;
+  const int64_t B3 = (int64_t)B * B * B;
+  const int64_t ng = blockIdx.x;
+  const int l = (int)(ng / N3);
+  const int node = (int)(ng % N3);
+  const int nx = node / (N * N), ny = (node / N) % N, nz = node % N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t my_child = 0, my_tile = 0, my_in = 0;
+  for (int j = 0; j < 32; ++j) {
+    const int cell = (warp * 32 + j) * 32 + lane;
+    const int bx = nx * 16 + (cell >> 8), by = ny * 16 + ((cell >> 4) & 15),
+              bz = nz * 16 + (cell & 15);
+    const bool in = bx < B && by < B && bz < B;
+    uint8_t st = kBlockEmpty;
+    if (in) st = blk_state[(int64_t)l * B3 + ((int64_t)bx * B + by) * B + bz];
+    const uint32_t c = __ballot_sync(kFull, st == kBlockPartial);
+    const uint32_t t = __ballot_sync(kFull, st == kBlockFull);
+    const uint32_t i = __ballot_sync(kFull, in);
+    if (lane == j) { my_child = c; my_tile = t; my_in = i; }
+  }
+  const int w = threadIdx.x;  // mask word 0..127
+  child[ng * kNodeWords + w] = my_child;
+  tile[ng * kNodeWords + w] = my_tile;
+  uint32_t leaves = 0, tiles = 0, incells = 0;
+  local_prefix[ng * kNodeWords + w] = cta_exclusive_scan(__popc(my_child), warp_tot, &leaves);
+  cta_exclusive_scan(__popc(my_tile), warp_tot, &tiles);
+  cta_exclusive_scan(__popc(my_in), warp_tot, &incells);
+  if (threadIdx.x == 0) {
+    node_leaves[ng] = leaves;
+    node_tiles[ng] = tiles;
+    uint32_t st = kNodeMixed;
+    if (leaves == 0 && tiles == 0) st = kNodeEmpty;
+    else if (leaves == 0 && tiles == incells) st = kNodeFull;
+    nstate[ng] = st;
+  }
+}
+
+constexpr int kMaxNodesTotal = HDDA_MAX_LEVELS * (HDDA_MAX_RES / kNodeVox) *
+                               (HDDA_MAX_RES / kNodeVox) * (HDDA_MAX_RES / kNodeVox);
+
+__global__ void vdb_finalize_kernel(int64_t nodes, const uint32_t* __restrict__ node_leaves,
+                                    const uint32_t* __restrict__ node_tiles,
+                                    const uint32_t* __restrict__ local_prefix,
+                                    uint32_t* __restrict__ prefix, int64_t* __restrict__ totals) {
+  __shared__ uint32_t base[kMaxNodesTotal];
+  __shared__ uint32_t warp_tot[33];
+  uint32_t carry = 0, tiles = 0;
+  for (int64_t c0 = 0; c0 < nodes; c0 += blockDim.x) {
+    const int64_t i = c0 + threadIdx.x;
+    const uint32_t v = i < nodes ? node_leaves[i] : 0u;
+    uint32_t chunk = 0;
+    const uint32_t ex = cta_exclusive_scan(v, warp_tot, &chunk);
+    if (i < nodes) base[i] = carry + ex;
+    carry += chunk;
+    uint32_t tchunk = 0;
+    cta_exclusive_scan(i < nodes ? node_tiles[i] : 0u, warp_tot, &tchunk);
+    tiles += tchunk;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < nodes * kNodeWords; i += blockDim.x)
+    prefix[i] = base[i / kNodeWords] + local_prefix[i];
+  if (threadIdx.x == 0) {
+    totals[0] = carry;
+    totals[1] = tiles;
+  }
+}
+
+__global__ void vdb_scatter_kernel(int L, int B, int N, const uint8_t* __restrict__ blk_state,
+                                   const uint32_t* __restrict__ blk_masks,
+                                   const uint32_t* __restrict__ child,
+                                   const uint32_t* __restrict__ prefix,
+                                   uint32_t* __restrict__ leaves) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t blk = t >> 4;
+  const int part = (int)(t & 15);
+  const int64_t B3 = (int64_t)B * B * B;
+  if (blk >= (int64_t)L * B3) return;
+  if (blk_state[blk] != kBlockPartial) return;
+  const int l = (int)(blk / B3);
+  const int64_t b = blk % B3;
+  const int bx = (int)(b / ((int64_t)B * B)), by = (int)((b / B) % B), bz = (int)(b % B);
+  const int node = ((bx >> 4) * N + (by >> 4)) * N + (bz >> 4);
+  const int64_t ng = (int64_t)l * N * N * N + node;
+  const int cell = ((bx & 15) * 16 + (by & 15)) * 16 + (bz & 15);
+  const int w = cell >> 5;
+  const uint32_t bit = 1u << (cell & 31);
+  const uint32_t leaf = prefix[ng * kNodeWords + w] + __popc(child[ng * kNodeWords + w] & (bit - 1u));
+  leaves[(int64_t)leaf * kLeafWords + part] = blk_masks[blk * kLeafWords + part];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+int validate(const uint8_t* dense, int levels, int res, const hdda_aabb* aabbs) {
+  if (!dense) return set_error(HDDA_ERR_INVALID_ARG, "dense is NULL");
+  if (!aabbs) return set_error(HDDA_ERR_INVALID_ARG, "aabbs is NULL");
+  if (levels < 1 || levels > HDDA_MAX_LEVELS)
+    return set_error(HDDA_ERR_INVALID_ARG, "levels=%d outside 1..%d", levels, HDDA_MAX_LEVELS);
+  if (res < 1 || res > HDDA_MAX_RES)
+    return set_error(HDDA_ERR_INVALID_ARG, "res=%d outside 1..%d", res, HDDA_MAX_RES);
+  for (int l = 0; l < levels; ++l) {
+    for (int c = 0; c < 3; ++c) {
+      const float lo = aabbs[l].lo[c], hi = aabbs[l].hi[c];
+      if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi))
+        return set_error(HDDA_ERR_INVALID_ARG, "level %d axis %d: box [%g, %g) invalid", l, c,
+                         (double)lo, (double)hi);
+      const float s = (float)res / (hi - lo);
+      if (!std::isfinite(s))
+        return set_error(HDDA_ERR_INVALID_ARG, "level %d axis %d: scale not finite", l, c);
+    }
+  }
+  return HDDA_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T>
+void carve(char* base, size_t& off, T*& ptr, int64_t count, bool take) {
+  if (take) {
+    ptr = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off = align_up(off + sizeof(T) * (size_t)count);
+  } else {
+    ptr = nullptr;
+  }
+}
+
+size_t layout(hdda_grid* g, char* base) {
+  const bool vdb = g->kind == HDDA_GRID_VDB;
+  size_t off = 0;
+  carve(base, off, g->thr, g->thr_count(), true);
+  carve(base, off, g->bits, (int64_t)g->L * g->W, !vdb);
+  const int64_t nw = g->nodes_total() * kNodeWords;
+  carve(base, off, g->child, nw, vdb);
+  carve(base, off, g->tile, nw, vdb);
+  carve(base, off, g->prefix, nw, vdb);
+  carve(base, off, g->nstate, g->nodes_total(), vdb);
+  carve(base, off, g->leaves, g->blocks_total() * kLeafWords, vdb);
+  carve(base, off, g->blk_masks, g->blocks_total() * kLeafWords, vdb);
+  carve(base, off, g->blk_state, g->blocks_total(), vdb);
+  carve(base, off, g->local_prefix, nw, vdb);
+  carve(base, off, g->node_leaves, g->nodes_total(), vdb);
+  carve(base, off, g->node_tiles, g->nodes_total(), vdb);
+  carve(base, off, g->totals, 2, vdb);
+  return off;
+}
+
+unsigned blocks_for(int64_t threads, int per) { return (unsigned)((threads + per - 1) / per); }
+
+int launch_build(hdda_grid* g, const uint8_t* dense, cudaStream_t s) {
+  if (g->kind == HDDA_GRID_DENSE) {
+    const int64_t words = (int64_t)g->L * g->W;
+    KernelTimer kt("pack_dense", s);
+    pack_dense_kernel<<<blocks_for(words, 256), 256, 0, s>>>(dense, g->L, g->R, g->W, g->bits);
+    kt.stop();
+    HDDA_CUDA_TRY(cudaGetLastError());
+  } else {
+    const int64_t nblk = g->blocks_total();
+    KernelTimer kt("build_vdb", s);  // the four build kernels together
+    vdb_blocks_kernel<<<blocks_for(nblk * 32, 256), 256, 0, s>>>(dense, g->L, g->R, g->B,
+                                                                 g->blk_masks, g->blk_state);
+    HDDA_CUDA_TRY(cudaGetLastError());
+    vdb_nodes_kernel<<<(unsigned)g->nodes_total(), kNodeWords, 0, s>>>(
+        g->L, g->B, g->N, g->blk_state, g->child, g->tile, g->local_prefix, g->node_leaves,
+        g->node_tiles, g->nstate);
+    HDDA_CUDA_TRY(cudaGetLastError());
+    vdb_finalize_kernel<<<1, 1024, 0, s>>>(g->nodes_total(), g->node_leaves, g->node_tiles,
+                                          g->local_prefix, g->prefix, g->totals);
+    HDDA_CUDA_TRY(cudaGetLastError());
+    vdb_scatter_kernel<<<blocks_for(nblk * 16, 256), 256, 0, s>>>(
+        g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves);
+    kt.stop();
+    HDDA_CUDA_TRY(cudaGetLastError());
+  }
+  HDDA_CUDA_TRY(cudaEventRecord(g->built, s));
+  return HDDA_OK;
+}
+
+int create(int kind, const uint8_t* dense, int levels, int res, const hdda_aabb* aabbs,
+           hdda_grid** out, cudaStream_t s) {
+  clear_error();
+  if (!out) return set_error(HDDA_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int st = validate(dense, levels, res, aabbs);
+  if (st != HDDA_OK) return st;
+  hdda_grid* g = new (std::nothrow) hdda_grid();
+  if (!g) return set_error(HDDA_ERR_OOM, "host allocation failed");
+  g->kind = kind;
+  g->L = levels;
+  g->R = res;
+  g->B = (res + kBlockDim - 1) / kBlockDim;
+  g->N = (g->B + kNodeDim - 1) / kNodeDim;
+  g->W = (int)(((int64_t)res * res * res + 31) / 32);
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) { delete g; return cuda_error(e, "cudaGetDevice"); }
+  for (int l = 0; l < levels; ++l) {
+    g->boxes[l] = aabbs[l];
+    for (int c = 0; c < 3; ++c) g->scale[l][c] = (float)res / (aabbs[l].hi[c] - aabbs[l].lo[c]);
+  }
+  g->base_bytes = layout(g, nullptr);
+  e = cudaMalloc(&g->base, g->base_bytes);
+  if (e != cudaSuccess) { delete g; return cuda_error(e, "cudaMalloc(grid)"); }
+  layout(g, static_cast<char*>(g->base));
+  e = cudaEventCreateWithFlags(&g->built, cudaEventDisableTiming);
+  if (e != cudaSuccess) { hdda_grid_free(g); return cuda_error(e, "cudaEventCreate"); }
+  thresholds_kernel<<<blocks_for(g->thr_count(), 128), 128, 0, s>>>(g->view(), g->thr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { hdda_grid_free(g); return cuda_error(e, "thresholds_kernel"); }
+  st = launch_build(g, dense, s);
+  if (st != HDDA_OK) { hdda_grid_free(g); return st; }
+  *out = g;
+  return HDDA_OK;
+}
+
+int64_t structure_bytes(const hdda_grid* g, int64_t n_leaves) {
+  int64_t b = (int64_t)g->L * (int64_t)sizeof(LevelDev) + g->thr_count() * 4;
+  if (g->kind == HDDA_GRID_DENSE) {
+    b += (int64_t)g->L * g->W * 4;
+  } else {
+    b += g->nodes_total() * (3 * kNodeWords * 4 + 4);
+    b += n_leaves * kLeafWords * 4;
+  }
+  return b;
+}
+
+}  // namespace
+}  // namespace hdda
+
+using namespace hdda;
+
+extern "C" int hdda_pack_dense(const uint8_t* dense, int levels, int res, const hdda_aabb* aabbs,
+                               hdda_grid** out, hdda_stream_t stream) {
+  return create(HDDA_GRID_DENSE, dense, levels, res, aabbs, out, (cudaStream_t)stream);
+}
+
+extern "C" int hdda_build_vdb(const uint8_t* dense, int levels, int res, const hdda_aabb* aabbs,
+                              hdda_grid** out, size_t* bytes_out, hdda_stream_t stream) {
+  int st = create(HDDA_GRID_VDB, dense, levels, res, aabbs, out, (cudaStream_t)stream);
+  if (st != HDDA_OK || !bytes_out) return st;
+  hdda_grid_stats gs;
+  st = hdda_grid_stats_get(*out, &gs);
+  if (st != HDDA_OK) return st;
+  *bytes_out = (size_t)gs.bytes;
+  return HDDA_OK;
+}
+
+extern "C" int hdda_grid_rebuild(hdda_grid* grid, const uint8_t* dense, hdda_stream_t stream) {
+  clear_error();
+  if (!grid) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
+  if (!dense) return set_error(HDDA_ERR_INVALID_ARG, "dense is NULL");
+  return launch_build(grid, dense, (cudaStream_t)stream);
+}
+
+extern "C" int hdda_grid_stats_get(const hdda_grid* g, hdda_grid_stats* out) {
+  clear_error();
+  if (!g || !out) return set_error(HDDA_ERR_INVALID_ARG, "grid or out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  out->kind = g->kind;
+  out->levels = g->L;
+  out->res = g->R;
+  out->blocks = g->B;
+  out->nodes = g->N;
+  out->dense_bytes = (int64_t)g->L * g->W * 4;
+  int64_t totals[2] = {0, 0};
+  if (g->kind == HDDA_GRID_VDB) {
+    HDDA_CUDA_TRY(cudaEventSynchronize(g->built));
+    HDDA_CUDA_TRY(cudaMemcpy(totals, g->totals, sizeof(totals), cudaMemcpyDeviceToHost));
+  }
+  out->n_leaves = totals[0];
+  out->n_tiles = totals[1];
+  out->bytes = structure_bytes(g, totals[0]);
+  return HDDA_OK;
+}
+
+extern "C" int hdda_grid_copy_array(const hdda_grid* g, int which, void* dst, size_t bytes,
+                                    size_t* needed) {
+  clear_error();
+  if (!g) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
+  const bool vdb = g->kind == HDDA_GRID_VDB;
+  const void* src = nullptr;
+  size_t n = 0;
+  const size_t nw = (size_t)g->nodes_total() * kNodeWords * 4;
+  switch (which) {
+    case HDDA_ARRAY_THRESHOLDS: src = g->thr; n = (size_t)g->thr_count() * 4; break;
+    case HDDA_ARRAY_DENSE_BITS: if (!vdb) { src = g->bits; n = (size_t)g->L * g->W * 4; } break;
+    case HDDA_ARRAY_CHILD_MASK: if (vdb) { src = g->child; n = nw; } break;
+    case HDDA_ARRAY_TILE_MASK: if (vdb) { src = g->tile; n = nw; } break;
+    case HDDA_ARRAY_LEAF_PREFIX: if (vdb) { src = g->prefix; n = nw; } break;
+    case HDDA_ARRAY_LEAVES:
+      if (vdb) {
+        hdda_grid_stats gs;
+        int st = hdda_grid_stats_get(g, &gs);
+        if (st != HDDA_OK) return st;
+        src = g->leaves;
+        n = (size_t)gs.n_leaves * kLeafWords * 4;
+      }
+      break;
+    default: break;
+  }
+  if (!src) return set_error(HDDA_ERR_INVALID_ARG, "array %d not held by this grid", which);
+  if (needed) *needed = n;
+  if (!dst) return HDDA_OK;
+  if (bytes < n) return set_error(HDDA_ERR_CAPACITY, "array needs %zu bytes, got %zu", n, bytes);
+  HDDA_CUDA_TRY(cudaEventSynchronize(g->built));
+  if (n) HDDA_CUDA_TRY(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
+  return HDDA_OK;
+}
+
+extern "C" void hdda_grid_free(hdda_grid* g) {
+  if (!g) return;
+  if (g->built) {
+    cudaEventSynchronize(g->built);
+    cudaEventDestroy(g->built);
+  }
+  if (g->base) {
+    cudaDeviceSynchronize();
+    cudaFree(g->base);
+  }
+  delete g;
+}

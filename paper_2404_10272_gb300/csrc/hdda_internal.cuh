@@ -1,0 +1,109 @@
+// hdda_internal.cuh -- device-side views, status helpers and the exact
+// binary32 point arithmetic shared by the grid builders and the samplers.
+//
+// Every float operation that decides a sample goes through __fadd_rn /
+// __fsub_rn / __fmul_rn, which the compiler never contracts into a fused
+// multiply-add, and the translation units that use them are also compiled
+// with -fmad=false.  Together with IEEE round-to-nearest on both sides this
+// makes the samplers reproduce the binary32 definition exactly.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hdda.h"
+
+namespace hdda {
+
+constexpr int kMaxLevels = HDDA_MAX_LEVELS;
+constexpr int kBlockDim = 8;     // leaf block edge (8^3 voxels)
+constexpr int kNodeDim = 16;     // node edge in blocks (16^3 blocks)
+constexpr int kNodeVox = kBlockDim * kNodeDim;  // 128 voxels per node edge
+constexpr int kNodeWords = 4096 / 32;           // 128 mask words per node
+constexpr int kLeafWords = 512 / 32;            // 16 words per leaf
+
+enum NodeState : uint32_t { kNodeEmpty = 0, kNodeMixed = 1, kNodeFull = 2 };
+enum BlockState : uint8_t { kBlockEmpty = 0, kBlockPartial = 1, kBlockFull = 2 };
+
+// Status bits a kernel may raise in a device status word.
+enum DeviceStatus : uint32_t {
+  kDevOk = 0,
+  kDevStepLimit = 1u << 0,
+  kDevInternal = 1u << 1,
+  kDevCapacity = 1u << 2,
+};
+
+struct LevelDev {
+  float lo[3];
+  float hi[3];
+  float s[3];  // fl32(res / fl32(hi - lo))
+};
+
+// Everything a traversal kernel needs to know about a grid, passed by value
+// as a kernel parameter (it lives in the constant bank).
+struct GridDev {
+  int kind;
+  int L, R, B, N;
+  int W;                     // dense bit words per level
+  LevelDev lv[kMaxLevels];
+  const float* thr;          // [L][3][R+1] exact index thresholds
+  const uint32_t* bits;      // dense: [L][W]
+  const uint32_t* child;     // vdb: [L*N^3][128]
+  const uint32_t* tile;      // vdb: [L*N^3][128]
+  const uint32_t* prefix;    // vdb: [L*N^3][128] global leaf index per word
+  const uint32_t* nstate;    // vdb: [L*N^3]
+  const uint32_t* leaves;    // vdb: [n_leaves][16]
+};
+
+// The lattice shared by every ray of a call: t[0..K], tm[0..K-1].
+struct LatticeDev {
+  const float* t;
+  const float* tm;
+  int K;
+};
+
+__device__ __forceinline__ int voxel_index(float x, float lo, float s, int R) {
+  float u = __fmul_rn(__fsub_rn(x, lo), s);
+  int i = (int)floorf(u);
+  return min(max(i, 0), R - 1);
+}
+
+// Order-preserving map between binary32 values and uint32 keys.
+__device__ __forceinline__ uint32_t float_key(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+}  // namespace hdda
+
+// ---------------------------------------------------------------------------
+// host-side helpers (runtime.cu)
+// ---------------------------------------------------------------------------
+namespace hdda {
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+void clear_error();
+
+// Brackets one kernel launch with events when the profiler is enabled.
+class KernelTimer {
+ public:
+  KernelTimer(const char* name, cudaStream_t s);
+  void stop();
+  ~KernelTimer() { stop(); }
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr;
+  bool live_ = false;
+};
+}  // namespace hdda
+
+#define HDDA_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return ::hdda::cuda_error(_e, #expr); \
+  } while (0)

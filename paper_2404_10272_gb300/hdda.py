@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libhdda (``include/hdda.h``).
+
+Argument marshalling only: every step of the sampler runs in the CUDA
+library.  Tensors are torch CUDA tensors (device memory and streams come
+from PyTorch); calls run on the current torch stream.  There is no CPU
+fallback: if the library is not built, or a call fails, an exception says
+so.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_STEP_LIMIT, ERR_TIMEOUT, ERR_OOM, ERR_INTERNAL = range(1, 8)
+GRID_DENSE, GRID_VDB = 0, 1
+ARRAY_THRESHOLDS, ARRAY_DENSE_BITS, ARRAY_CHILD_MASK, ARRAY_TILE_MASK, ARRAY_LEAF_PREFIX, ARRAY_LEAVES = range(6)
+
+EXPORTED = [
+    "hdda_version", "hdda_last_error", "hdda_pack_dense", "hdda_build_vdb", "hdda_grid_rebuild",
+    "hdda_grid_stats_get", "hdda_grid_copy_array", "hdda_grid_free", "hdda_traverse_dense",
+    "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
+]
+
+
+class HddaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libhdda status {code}: {msg}")
+        self.code = code
+
+
+class AABB(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("near_t", ctypes.c_float), ("far_t", ctypes.c_float), ("step", ctypes.c_float),
+                ("cone_angle", ctypes.c_float), ("max_step", ctypes.c_float),
+                ("max_steps", ctypes.c_int32)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+class GridStats(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32), ("res", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("nodes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("bytes", ctypes.c_int64),
+                ("dense_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.library_path()
+
+
+def load(path: str | None = None):
+    """Loads libhdda.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libhdda is not built ({p} missing): run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    lib.hdda_version.restype = ctypes.c_char_p
+    lib.hdda_last_error.restype = ctypes.c_char_p
+    lib.hdda_pack_dense.argtypes = [vp, i32, i32, ctypes.POINTER(AABB), ctypes.POINTER(vp), vp]
+    lib.hdda_build_vdb.argtypes = [vp, i32, i32, ctypes.POINTER(AABB), ctypes.POINTER(vp),
+                                   ctypes.POINTER(sz), vp]
+    lib.hdda_grid_rebuild.argtypes = [vp, vp, vp]
+    lib.hdda_grid_stats_get.argtypes = [vp, ctypes.POINTER(GridStats)]
+    lib.hdda_grid_copy_array.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
+    lib.hdda_grid_free.argtypes = [vp]
+    lib.hdda_grid_free.restype = None
+    trav = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp]
+    lib.hdda_traverse_dense.argtypes = trav
+    lib.hdda_traverse_hdda.argtypes = trav
+    lib.hdda_composite.argtypes = [vp, vp, i64, vp, vp, vp, vp, i32, vp, vp]
+    lib.hdda_profiler_enable.argtypes = [i32]
+    lib.hdda_profiler_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
+    for name in EXPORTED:
+        if name not in ("hdda_version", "hdda_last_error", "hdda_grid_free"):
+            getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != OK:
+        raise HddaError(code, load().hdda_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _cuda(t, dtype, shape=None):
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t))
+    if t.device.type != "cuda" or t.dtype != dtype or not t.is_contiguous():
+        t = t.to(device="cuda", dtype=dtype).contiguous()
+    if shape is not None:
+        t = t.reshape(shape)
+    return t
+
+
+def _aabbs(aabbs, levels):
+    a = np.asarray(aabbs, np.float32).reshape(levels, 6)
+    arr = (AABB * levels)()
+    for l in range(levels):
+        arr[l].lo[:] = [float(v) for v in a[l, :3]]
+        arr[l].hi[:] = [float(v) for v in a[l, 3:]]
+    return arr
+
+
+def make_params(near, far, step, cone=0.0, max_step=1e10, max_steps=1 << 20) -> Params:
+    return Params(near, far, step, cone, max_step, max_steps)
+
+
+class Grid:
+    """A library-owned device grid (dense bit array or VDB tree)."""
+
+    def __init__(self, handle, kind, levels, res):
+        self._h = handle
+        self.kind, self.levels, self.res = kind, levels, res
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> GridStats:
+        st = GridStats()
+        _check(load().hdda_grid_stats_get(self._h, ctypes.byref(st)))
+        return st
+
+    def array(self, which: int) -> np.ndarray:
+        need = ctypes.c_size_t(0)
+        _check(load().hdda_grid_copy_array(self._h, which, None, 0, ctypes.byref(need)))
+        dt = np.float32 if which == ARRAY_THRESHOLDS else np.uint32
+        out = np.zeros(need.value // 4, dt)
+        _check(load().hdda_grid_copy_array(self._h, which, out.ctypes.data_as(ctypes.c_void_p),
+                                           out.nbytes, ctypes.byref(need)))
+        return out
+
+    def rebuild(self, dense: torch.Tensor, stream=None):
+        d = _cuda(dense, torch.uint8)
+        _check(load().hdda_grid_rebuild(self._h, _ptr(d), _stream(stream)))
+
+    def free(self):
+        if self._h:
+            load().hdda_grid_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _dense_args(dense, aabbs):
+    d = _cuda(dense, torch.uint8)
+    if d.dim() == 3:
+        d = d.unsqueeze(0)
+    L, R = int(d.shape[0]), int(d.shape[1])
+    if tuple(d.shape) != (L, R, R, R):
+        raise ValueError(f"dense must be [L, R, R, R], got {tuple(d.shape)}")
+    return d, L, R, _aabbs(aabbs, L)
+
+
+def pack_dense(dense, aabbs, stream=None) -> Grid:
+    d, L, R, boxes = _dense_args(dense, aabbs)
+    h = ctypes.c_void_p()
+    _check(load().hdda_pack_dense(_ptr(d), L, R, boxes, ctypes.byref(h), _stream(stream)))
+    return Grid(h, GRID_DENSE, L, R)
+
+
+def build_vdb(dense, aabbs, stream=None) -> Grid:
+    d, L, R, boxes = _dense_args(dense, aabbs)
+    h = ctypes.c_void_p()
+    _check(load().hdda_build_vdb(_ptr(d), L, R, boxes, ctypes.byref(h), None, _stream(stream)))
+    return Grid(h, GRID_VDB, L, R)
+
+
+@dataclass
+class Samples:
+    offsets: torch.Tensor   # int64 [n+1]
+    ray_idx: torch.Tensor   # int32 [capacity] (first `total` valid)
+    t0: torch.Tensor        # float32 [capacity]
+    t1: torch.Tensor        # float32 [capacity]
+    total: int
+
+    def trimmed(self):
+        n = self.total
+        return self.offsets, self.ray_idx[:n], self.t0[:n], self.t1[:n]
+
+
+def alloc_samples(n_rays: int, capacity: int, device="cuda") -> Samples:
+    return Samples(offsets=torch.empty(n_rays + 1, dtype=torch.int64, device=device),
+                   ray_idx=torch.empty(capacity, dtype=torch.int32, device=device),
+                   t0=torch.empty(capacity, dtype=torch.float32, device=device),
+                   t1=torch.empty(capacity, dtype=torch.float32, device=device), total=0)
+
+
+def _traverse(fn_name, rays_o, rays_d, grid: Grid, params: Params, out: Samples | None,
+              count_only: bool, stream):
+    ro = _cuda(rays_o, torch.float32, (-1, 3))
+    rd = _cuda(rays_d, torch.float32, (-1, 3))
+    n = int(ro.shape[0])
+    fn = getattr(load(), fn_name)
+    total = ctypes.c_int64(0)
+    s = _stream(stream)
+    if out is None:
+        out = alloc_samples(n, 0, ro.device)
+        _check(fn(_ptr(ro), _ptr(rd), n, grid.handle, ctypes.byref(params), _ptr(out.offsets),
+                  None, None, None, 0, ctypes.byref(total), s))
+        out.total = total.value
+        if count_only:
+            return out
+        out = alloc_samples(n, max(1, total.value), ro.device)
+    cap = 0 if count_only else int(out.t0.numel())
+    code = fn(_ptr(ro), _ptr(rd), n, grid.handle, ctypes.byref(params), _ptr(out.offsets),
+              _ptr(out.ray_idx), _ptr(out.t0), _ptr(out.t1), cap, ctypes.byref(total), s)
+    out.total = total.value
+    _check(code)
+    return out
+
+
+def traverse_dense(rays_o, rays_d, grid: Grid, params: Params, out: Samples | None = None,
+                   count_only: bool = False, stream=None) -> Samples:
+    """Dense-grid DDA sampler.  Without `out`, counts first and allocates
+    exactly; with `out`, its capacity is used (HddaError ERR_CAPACITY if it
+    is too small)."""
+    return _traverse("hdda_traverse_dense", rays_o, rays_d, grid, params, out, count_only, stream)
+
+
+def traverse_hdda(rays_o, rays_d, grid: Grid, params: Params, out: Samples | None = None,
+                  count_only: bool = False, stream=None) -> Samples:
+    """Hierarchical-DDA sampler over a VDB grid (same contract)."""
+    return _traverse("hdda_traverse_hdda", rays_o, rays_d, grid, params, out, count_only, stream)
+
+
+def composite(rays_o, rays_d, samples: Samples, field, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    ro = _cuda(rays_o, torch.float32, (-1, 3))
+    rd = _cuda(rays_d, torch.float32, (-1, 3))
+    f = _cuda(field, torch.float32, (-1, 8))
+    n = int(ro.shape[0])
+    if out is None:
+        out = torch.empty((n, 4), dtype=torch.float32, device=ro.device)
+    _check(load().hdda_composite(_ptr(ro), _ptr(rd), n, _ptr(samples.offsets), _ptr(samples.t0),
+                                 _ptr(samples.t1), _ptr(f), int(f.shape[0]), _ptr(out),
+                                 _stream(stream)))
+    return out
+
+
+def profiler_enable(on: bool = True):
+    _check(load().hdda_profiler_enable(1 if on else 0))
+
+
+def profiler_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last read (synchronises)."""
+    cap = 64
+    arr = (KernelTime * cap)()
+    n = ctypes.c_int(0)
+    _check(load().hdda_profiler_read(arr, cap, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
+            for i in range(min(n.value, cap))}

@@ -23,7 +23,9 @@ Conventions shared by every generator:
 """
 from __future__ import annotations
 
+import copy
 from dataclasses import dataclass, field as dc_field
+import functools
 import math
 
 import numpy as np
@@ -218,6 +220,17 @@ def _shells(rng, n, c_range, a_range):
     return centres, axes, rots
 
 
+def _cached_scene(fn):
+    """Scenes take seconds to generate; keep one per argument set and hand out copies."""
+    cached = functools.lru_cache(maxsize=8)(fn)
+
+    @functools.wraps(fn)
+    def wrapper(*args, **kwargs):
+        return copy.deepcopy(cached(*args, **kwargs))
+    return wrapper
+
+
+@_cached_scene
 def tiny_scene(seed: int = 1001) -> Scene:
     """One 64^3 level over [-1.5, 1.5)^3; shells of 3 random ellipsoids
     (voxel centres within 0.05 of a surface); near 2, far 6, step 5e-3."""
@@ -235,6 +248,7 @@ def tiny_camera(seed: int = 1001) -> Camera:
     return orbit_camera(np.random.default_rng(seed + 1), 4.0, 96, 96, 0.69)
 
 
+@_cached_scene
 def object_scene(seed: int = 1002, R: int = 128) -> Scene:
     """One 128^3 level over [-1.5, 1.5)^3: 8 thin ellipsoidal shells plus 2
     solid ellipsoids, dilated by one voxel; near 2, far 6,
@@ -257,6 +271,7 @@ def object_cameras(seed: int = 1002, n: int = 20, W: int = 800, H: int = 800) ->
     return [orbit_camera(np.random.default_rng(seed + 1 + j), 4.0, W, H, 0.69) for j in range(n)]
 
 
+@_cached_scene
 def unbounded_scene(seed: int = 1003, levels: int = 4, R: int = 128) -> Scene:
     """Four 128^3 cascade levels, level l over [-2^l, 2^l)^3: ellipsoidal
     shells at the centre of level 0 and random axis-aligned boxes in the

@@ -1,0 +1,53 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/hdda.h declares.  No compute call is made (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hdda.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hdda_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2404_10272_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["hdda_pack_dense", "hdda_build_vdb", "hdda_traverse_dense",
+                     "hdda_traverse_hdda", "hdda_composite", "hdda_last_error", "hdda_grid_free"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in hdda.h but not exported"
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (hdda_[a-z_0-9]+)$", out, flags=re.M))
+    assert exported == set(declared_functions()), exported ^ set(declared_functions())
+
+
+def test_version_and_error_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.hdda_version.restype = ctypes.c_char_p
+    lib.hdda_last_error.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.hdda_version()
+    assert lib.hdda_last_error() == b""
+
+
+def test_binding_names_match_header():
+    from paper_2404_10272_gb300 import hdda
+    assert sorted(hdda.EXPORTED) == declared_functions()
+
