@@ -226,6 +226,31 @@ int hdda_traverse_hdda(const float* rays_o, const float* rays_d, int64_t n_rays,
                        int64_t* total_out, hdda_stream_t stream);
 
 /*
+ * Hierarchical-DDA sampler that allocates nothing, for callers that must not
+ * allocate GPU memory: applications that reserve all device memory up front
+ * and hand libraries fixed buffers, or loops that must never enter the CUDA
+ * allocator.  The paper has no counterpart; it is a deployment variant of
+ * hdda_traverse_hdda with the same arguments and the same results.
+ *
+ * Its per-call scratch (lattice table, per-CTA sums and counters) lives in
+ * one fixed device array of 393,728 bytes inside the library, present on
+ * every GPU that loads the library until the process exits; the lattice is
+ * recomputed on every call instead of being cached.  Limits, rejected with
+ * HDDA_ERR_INVALID_ARG and a message: n_rays <= 2,097,152 and at most
+ * 16,384 lattice candidates per ray.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array: calls whose GPU work overlaps race on it and must
+ * be serialised by the caller.  Synchronises the stream twice (lattice
+ * length, sample total); the emission is left in flight.
+ */
+int hdda_traverse_hdda_noalloc(const float* rays_o, const float* rays_d, int64_t n_rays,
+                               const hdda_grid* grid, const hdda_params* params,
+                               int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
+                               int64_t capacity, int64_t* total_out, hdda_stream_t stream);
+
+/*
  * Front-to-back compositing of the kept intervals over a Gaussian-blob field
  * (Sec. 1: densities and colours of the sampled points are accumulated into
  * the pixel).  For each ray, in order of its samples, with x the position at

@@ -27,6 +27,7 @@ SOURCES = {
     "grid.cu": ["-fmad=false"],
     "traverse.cu": ["-fmad=false"],
     "composite.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -100,6 +100,17 @@ class KernelTimer {
   cudaEvent_t a_ = nullptr;
   bool live_ = false;
 };
+// Traversal over scratch memory the caller provides instead of memory the
+// library allocates (traverse.cu).  `scratch` is device memory of at least
+// traverse_scratch_bytes(max_k, max_tiles) bytes, 256-byte aligned; nothing
+// is allocated.  Rays per tile: traverse_rays_per_tile().
+size_t traverse_scratch_bytes(int max_k, int64_t max_tiles);
+int64_t traverse_rays_per_tile();
+int traverse_with_scratch(bool vdb, const float* ro, const float* rd, int64_t n,
+                          const struct ::hdda_grid* grid, const hdda_params* params,
+                          int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
+                          int64_t capacity, int64_t* total_out, void* scratch, int max_k,
+                          int64_t max_tiles, cudaStream_t s);
 }  // namespace hdda
 
 #define HDDA_CUDA_TRY(expr)                                   \

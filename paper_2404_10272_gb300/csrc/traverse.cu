@@ -578,6 +578,126 @@ int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_g
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// traversal over caller-provided scratch (no allocation of any kind)
+// ---------------------------------------------------------------------------
+// Scratch layout: [0,256) header {ticket u32, status u32, total i64,
+// lattice count i64, lattice limit flag i64}; then t[max_k + 1] and
+// tm[max_k] floats; then tile_sum[max_tiles] and tile_prefix[max_tiles].
+
+namespace {
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+size_t traverse_scratch_bytes(int max_k, int64_t max_tiles) {
+  return 256 + align256(sizeof(float) * (2 * (size_t)max_k + 1)) +
+         2 * sizeof(int64_t) * (size_t)max_tiles;
+}
+
+int64_t traverse_rays_per_tile() { return kBS; }
+
+int traverse_with_scratch(bool vdb, const float* ro, const float* rd, int64_t n,
+                          const hdda_grid* grid, const hdda_params* params, int64_t* offsets,
+                          int32_t* ray_idx, float* t0, float* t1, int64_t capacity,
+                          int64_t* total_out, void* scratch, int max_k, int64_t max_tiles,
+                          cudaStream_t s) {
+  clear_error();
+  if (!grid) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
+  if (grid->kind != (vdb ? HDDA_GRID_VDB : HDDA_GRID_DENSE))
+    return set_error(HDDA_ERR_INVALID_ARG, vdb ? "hdda traversal needs a VDB grid"
+                                               : "dense traversal needs a dense grid");
+  if (n < 0 || n > INT32_MAX) return set_error(HDDA_ERR_INVALID_ARG, "n_rays=%lld", (long long)n);
+  const int64_t nb = (n + kBS - 1) / kBS;
+  if (nb > max_tiles)
+    return set_error(HDDA_ERR_INVALID_ARG,
+                     "n_rays=%lld exceeds the static scratch maximum of %lld rays",
+                     (long long)n, (long long)(max_tiles * kBS));
+  if (!offsets || !total_out) return set_error(HDDA_ERR_INVALID_ARG, "offsets/total_out NULL");
+  if (n > 0 && (!ro || !rd)) return set_error(HDDA_ERR_INVALID_ARG, "rays NULL");
+  if (capacity < 0) return set_error(HDDA_ERR_INVALID_ARG, "capacity < 0");
+  if (capacity > 0 && (!ray_idx || !t0 || !t1))
+    return set_error(HDDA_ERR_INVALID_ARG, "sample outputs NULL with capacity > 0");
+  if (!scratch) return set_error(HDDA_ERR_INVALID_ARG, "scratch is NULL");
+  int st = validate_params(params);
+  if (st != HDDA_OK) return st;
+  int dev = 0;
+  HDDA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != grid->device)
+    return set_error(HDDA_ERR_INVALID_ARG, "grid lives on device %d, current is %d",
+                     grid->device, dev);
+  *total_out = 0;
+
+  char* base = static_cast<char*>(scratch);
+  unsigned* ticket = reinterpret_cast<unsigned*>(base);
+  unsigned* status = ticket + 1;
+  int64_t* total = reinterpret_cast<int64_t*>(base + 8);
+  int64_t* lat_words = reinterpret_cast<int64_t*>(base + 16);
+  float* lat_t = reinterpret_cast<float*>(base + 256);
+  float* lat_tm = lat_t + max_k + 1;
+  int64_t* tile_sum =
+      reinterpret_cast<int64_t*>(base + 256 + align256(sizeof(float) * (2 * (size_t)max_k + 1)));
+  int64_t* tile_prefix = tile_sum + max_tiles;
+
+  // The array keeps the previous call's contents: clear the counters first.
+  HDDA_CUDA_TRY(cudaMemsetAsync(base, 0, 32, s));
+  hdda_params key;
+  std::memset(&key, 0, sizeof(key));
+  key.near_t = params->near_t; key.far_t = params->far_t; key.step = params->step;
+  key.cone_angle = params->cone_angle; key.max_step = params->max_step;
+  key.max_steps = params->max_steps;
+  lattice_count_kernel<<<1, 1, 0, s>>>(key, lat_words);
+  HDDA_CUDA_TRY(cudaGetLastError());
+  int64_t hw[2] = {0, 0};  // pageable host words: no host allocation either
+  HDDA_CUDA_TRY(cudaMemcpyAsync(hw, lat_words, sizeof(hw), cudaMemcpyDeviceToHost, s));
+  HDDA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hw[1])
+    return set_error(HDDA_ERR_STEP_LIMIT, "lattice has more than max_steps=%d candidates",
+                     params->max_steps);
+  if (hw[0] > max_k)
+    return set_error(HDDA_ERR_INVALID_ARG,
+                     "lattice of %lld candidates exceeds the static scratch maximum of %d",
+                     (long long)hw[0], max_k);
+  const LatticeDev lat{lat_t, lat_tm, (int)hw[0]};
+  lattice_fill_kernel<<<1, 1, 0, s>>>(key, lat.K, lat_t, lat_tm);
+  HDDA_CUDA_TRY(cudaGetLastError());
+  if (n == 0) {
+    HDDA_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
+    return HDDA_OK;
+  }
+  const GridDev g = grid->view();
+  if (vdb)
+    count_kernel<true><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_sum,
+                                                    tile_prefix, ticket, status, total);
+  else
+    count_kernel<false><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_sum,
+                                                     tile_prefix, ticket, status, total);
+  HDDA_CUDA_TRY(cudaGetLastError());
+  HDDA_CUDA_TRY(cudaMemcpyAsync(hw, base, 16, cudaMemcpyDeviceToHost, s));
+  HDDA_CUDA_TRY(cudaStreamSynchronize(s));
+  const unsigned dev_status = reinterpret_cast<unsigned*>(hw)[1];
+  const int64_t tot = hw[1];
+  *total_out = tot;
+  if (dev_status & kDevInternal)
+    return set_error(HDDA_ERR_INTERNAL, "region check failed on the device");
+  if (capacity == 0) {
+    offsets_kernel<<<(unsigned)nb, kBS, 0, s>>>(n, offsets, tile_prefix, total);
+    HDDA_CUDA_TRY(cudaGetLastError());
+    return HDDA_OK;
+  }
+  if (capacity < tot)
+    return set_error(HDDA_ERR_CAPACITY, "capacity %lld < %lld samples", (long long)capacity,
+                     (long long)tot);
+  if (vdb)
+    emit_kernel<true><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_prefix,
+                                                   total, ray_idx, t0, t1, status);
+  else
+    emit_kernel<false><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_prefix,
+                                                    total, ray_idx, t0, t1, status);
+  HDDA_CUDA_TRY(cudaGetLastError());
+  return HDDA_OK;
+}
+
 }  // namespace hdda
 
 extern "C" int hdda_traverse_dense(const float* rays_o, const float* rays_d, int64_t n_rays,

@@ -26,6 +26,7 @@ EXPORTED = [
     "hdda_version", "hdda_last_error", "hdda_pack_dense", "hdda_build_vdb", "hdda_grid_rebuild",
     "hdda_grid_stats_get", "hdda_grid_copy_array", "hdda_grid_free", "hdda_traverse_dense",
     "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
+    "hdda_traverse_hdda_noalloc",
 ]
 
 
@@ -88,6 +89,7 @@ def load(path: str | None = None):
     trav = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp]
     lib.hdda_traverse_dense.argtypes = trav
     lib.hdda_traverse_hdda.argtypes = trav
+    lib.hdda_traverse_hdda_noalloc.argtypes = trav
     lib.hdda_composite.argtypes = [vp, vp, i64, vp, vp, vp, vp, i32, vp, vp]
     lib.hdda_profiler_enable.argtypes = [i32]
     lib.hdda_profiler_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
@@ -259,6 +261,24 @@ def traverse_hdda(rays_o, rays_d, grid: Grid, params: Params, out: Samples | Non
                   count_only: bool = False, stream=None) -> Samples:
     """Hierarchical-DDA sampler over a VDB grid (same contract)."""
     return _traverse("hdda_traverse_hdda", rays_o, rays_d, grid, params, out, count_only, stream)
+
+
+def traverse_hdda_noalloc(rays_o, rays_d, grid: Grid, params: Params, out: Samples,
+                          stream=None) -> Samples:
+    """Hierarchical-DDA sampler that allocates no memory of its own (static
+    device scratch inside the library).  `out` must be preallocated and
+    large enough; calls whose GPU work overlaps must be serialised."""
+    ro = _cuda(rays_o, torch.float32, (-1, 3))
+    rd = _cuda(rays_d, torch.float32, (-1, 3))
+    n = int(ro.shape[0])
+    total = ctypes.c_int64(0)
+    code = load().hdda_traverse_hdda_noalloc(
+        _ptr(ro), _ptr(rd), n, grid.handle, ctypes.byref(params), _ptr(out.offsets),
+        _ptr(out.ray_idx), _ptr(out.t0), _ptr(out.t1), int(out.t0.numel()), ctypes.byref(total),
+        _stream(stream))
+    out.total = total.value
+    _check(code)
+    return out
 
 
 def composite(rays_o, rays_d, samples: Samples, field, out: torch.Tensor | None = None,
