@@ -35,6 +35,11 @@ if ROOT not in sys.path:
 
 N_CAMERAS = 20
 L2_FLUSH_BYTES = 256 << 20
+# FP32-pipe instructions per blob evaluation in the compositor: 3 sub, 1 mul
+# + 2 fma (squared distance), 1 mul (exponent scale), 1 mul (amplitude),
+# 1 add (density), 3 fma (colour); the exp2 runs on the MUFU pipe alongside.
+COMPOSITE_FP32_PER_BLOB = 12
+KERNELS_PER_TIMER = {"build_vdb": 4}
 
 
 def parse_args():
@@ -46,6 +51,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-stride", type=int, default=16,
                     help="CPU baseline sample: every n-th ray of camera 0")
+    ap.add_argument("--profile-step", choices=["hdda", "dense"], default=None,
+                    help="profiling aid: one count-only call, one warm-up step and one step of "
+                         "the given path on camera 0, no timing, no JSON line")
     return ap.parse_args()
 
 
@@ -256,41 +264,62 @@ def run_ours(args):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    # FP32 pipe: 128 lanes per SM per clock at the maximum SM clock
+    alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
     S_avg = samples / K
     grid_bytes = int(vstats.bytes)
-    # algorithmic bytes per launch ("Roofline")
-    alg = {
-        "hdda_count": 24 * n + 8 * n + grid_bytes,
-        "hdda_emit": 8 * n + 8 * (n + 1) + 12 * S_avg,
-        "composite": 24 * n + 8 * (n + 1) + 8 * S_avg + 16 * n + 64 * 32,
+    G = int(sc.field.shape[0])
+    # algorithmic bytes (or FP32 instructions) per launch: see DESIGN.md, "Roofline"
+    sampler_bytes = 24 * n + 8 * (n + 1) + 12 * S_avg + grid_bytes
+    alg_bytes = {
+        "hdda_walk": 24 * n + grid_bytes,
+        "hdda_emit": 8 * (n + 1) + 12 * S_avg,
         "build_vdb": sc.occ.size + grid_bytes,
+        "composite": 24 * n + 8 * (n + 1) + 8 * S_avg + 16 * n + 32 * G,
     }
+    alg_inst = {"composite": S_avg * G * COMPOSITE_FP32_PER_BLOB}
     per_kernel = {}
     for name, (launches, tot_ms) in kern.items():
         avg = tot_ms / max(1, launches)
         ent = {"launches": launches, "avg_ms": round(avg, 4), "share": round(tot_ms / ms, 4)}
-        if name in alg:
-            ent["alg_bytes"] = int(alg[name])
-            ent["gbs"] = round(alg[name] / (avg / 1e3) / 1e9, 1)
+        if name in alg_bytes:
+            ent["alg_bytes"] = int(alg_bytes[name])
+            ent["gbs"] = round(alg_bytes[name] / (avg / 1e3) / 1e9, 1)
+        if name in alg_inst:
+            ent["tinst_s"] = round(alg_inst[name] / (avg / 1e3) / 1e12, 2)
         per_kernel[name] = ent
-    dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
-    roofline = None
-    if dom is not None:
-        launches, tot_ms = kern[dom]
-        avg = tot_ms / launches
-        ach = alg.get(dom, 0) / (avg / 1e3) / 1e9
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
-                    "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
-                    "peak_source": peak_src}
-    sam_launch = sum(kern.get(k, (1, 0.0))[1] / max(1, kern.get(k, (1, 0.0))[0])
-                     for k in ("hdda_count", "hdda_emit"))
-    sampler_alg = 24 * n + 8 * (n + 1) + 12 * S_avg + grid_bytes
-    roofline_sampler = {"kernels": ["hdda_count", "hdda_emit"], "bound": "hbm",
-                        "achieved": round(sampler_alg / (sam_launch / 1e3) / 1e9, 1),
-                        "peak": hbm_peak, "unit": "GB/s",
-                        "frac": round(sampler_alg / (sam_launch / 1e3) / 1e9 / hbm_peak, 4)}
 
-    launches_per_step = sum(v[0] for v in kern.values()) / K if kern else None
+    def roof(name):
+        launches, tot_ms = kern[name]
+        avg = tot_ms / max(1, launches)
+        if name in alg_inst:
+            ach = alg_inst[name] / (avg / 1e3) / 1e12
+            return {"kernel": name, "bound": "alu", "achieved": round(ach, 2),
+                    "peak": round(alu_peak, 2), "unit": "Tinst/s (FP32 pipe)",
+                    "frac": round(ach / alu_peak, 4), "traffic": None,
+                    "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock"}
+        ach = alg_bytes.get(name, 0) / (avg / 1e3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
+                "peak_source": peak_src}
+
+    dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
+    roofline = roof(dom) if dom else None
+    # the sampler as a whole (walk + emit): rays in, CSR offsets and samples out
+    sam_ms = sum(kern[k][1] / max(1, kern[k][0]) for k in ("hdda_walk", "hdda_emit") if k in kern)
+    roofline_sampler = None
+    if sam_ms > 0:
+        ach = sampler_bytes / (sam_ms / 1e3) / 1e9
+        roofline_sampler = {"kernels": ["hdda_walk", "hdda_emit"], "bound": "hbm",
+                            "alg_bytes": int(sampler_bytes), "ms": round(sam_ms, 4),
+                            "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                            "frac": round(ach / hbm_peak, 4), "peak_source": peak_src}
+
+    # the build_vdb timer spans the builder's four kernels; every other timer one kernel
+    launches_per_step = (sum(v[0] * KERNELS_PER_TIMER.get(k, 1) for k, v in kern.items()) / K
+                         if kern else None)
 
     # --- CPU oracle on a bounded sample (rank 0, N = 1) -------------------
     cpu = None
@@ -412,8 +441,40 @@ def run_reference(args):
     }), flush=True)
 
 
+def profile_step(args):
+    """Kernel launch order: sample (count only), build, sample, composite (warm-up),
+    build, sample, composite (the step to capture)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2404_10272_gb300 import hdda, scenes
+
+    sc = scenes.object_scene()
+    o, d = scenes.object_cameras(n=1)[0].rays()
+    O, D = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    dense = torch.from_numpy(sc.occ).cuda()
+    field = torch.from_numpy(sc.field).cuda()
+    p = sc.params
+    prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    vdb = args.profile_step == "hdda"
+    grid = hdda.build_vdb(dense, sc.aabbs) if vdb else hdda.pack_dense(dense, sc.aabbs)
+    trav = hdda.traverse_hdda if vdb else hdda.traverse_dense
+    cap = trav(O, D, grid, prm, count_only=True).total
+    bufs = hdda.alloc_samples(o.shape[0], cap)
+    rgba = torch.empty((o.shape[0], 4), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        grid.rebuild(dense)
+        s = trav(O, D, grid, prm, out=bufs)
+        hdda.composite(O, D, s, field, out=rgba)
+    torch.cuda.synchronize()
+    print(f"profile step done: {o.shape[0]} rays, {s.total} samples")
+
+
 def main():
     args = parse_args()
+    if args.profile_step:
+        profile_step(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -203,10 +203,11 @@ void hdda_grid_free(hdda_grid* grid);
  *                   intervals in ascending k
  *   capacity        0 = count only: offsets and *total_out are filled and
  *                   nothing else is written.  Otherwise, if capacity < total
- *                   the call returns HDDA_ERR_CAPACITY and writes no sample.
+ *                   the call returns HDDA_ERR_CAPACITY (with *total_out set)
+ *                   and writes no sample at or past index capacity.
  *   total_out       HOST int64: number of kept intervals
- * Synchronises the stream once (after counting, to read the total); the
- * emission that follows is left in flight on the stream.
+ * One kernel pass; the call synchronises the stream once at the end to read
+ * the total, so every output is complete when it returns.
  */
 int hdda_traverse_dense(const float* rays_o, const float* rays_d, int64_t n_rays,
                         const hdda_grid* grid, const hdda_params* params, int64_t* offsets,
@@ -243,7 +244,7 @@ int hdda_traverse_hdda(const float* rays_o, const float* rays_d, int64_t n_rays,
  * (cudaGetSymbolAddress) and should come before any stream capture.  All
  * calls share the array: calls whose GPU work overlaps race on it and must
  * be serialised by the caller.  Synchronises the stream twice (lattice
- * length, sample total); the emission is left in flight.
+ * length, sample total); every output is complete when it returns.
  */
 int hdda_traverse_hdda_noalloc(const float* rays_o, const float* rays_d, int64_t n_rays,
                                const hdda_grid* grid, const hdda_params* params,

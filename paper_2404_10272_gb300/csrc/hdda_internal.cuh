@@ -31,6 +31,7 @@ enum DeviceStatus : uint32_t {
   kDevStepLimit = 1u << 0,
   kDevInternal = 1u << 1,
   kDevCapacity = 1u << 2,
+  kDevTimeout = 1u << 3,
 };
 
 struct LevelDev {
@@ -55,12 +56,26 @@ struct GridDev {
   const uint32_t* leaves;    // vdb: [n_leaves][16]
 };
 
-// The lattice shared by every ray of a call: t[0..K], tm[0..K-1].
+// Buckets of the lattice's inverse index (t -> k), over binary32 keys.
+constexpr int kKidxMax = 2048;
+
+// The lattice shared by every ray of a call: t[0..K], tm[0..K-1] (interval
+// midpoints), and a bucket index kidx[0..NB+1] over the order-preserving
+// keys of tm: kidx[b] = first k with key(tm_k) >= key0 + (b << shift).
+// hdr = {key0, shift, NB} lives in device memory next to the tables.
 struct LatticeDev {
   const float* t;
   const float* tm;
+  const int* kidx;
+  const uint32_t* hdr;
   int K;
 };
+
+// Bytes of one lattice block of capacity max_k: t, tm, kidx and hdr.
+__host__ __device__ inline size_t lattice_block_bytes(int max_k) {
+  return (sizeof(float) * (2 * (size_t)max_k + 1) + sizeof(int) * (kKidxMax + 2) + 16 + 255) &
+         ~(size_t)255;
+}
 
 __device__ __forceinline__ int voxel_index(float x, float lo, float s, int R) {
   float u = __fmul_rn(__fsub_rn(x, lo), s);
@@ -91,7 +106,8 @@ void clear_error();
 // Brackets one kernel launch with events when the profiler is enabled.
 class KernelTimer {
  public:
-  KernelTimer(const char* name, cudaStream_t s);
+  // allow = false makes it a no-op (paths that must not create CUDA objects).
+  KernelTimer(const char* name, cudaStream_t s, bool allow = true);
   void stop();
   ~KernelTimer() { stop(); }
  private:

@@ -14,9 +14,11 @@
 //            16^3-block node, an empty or tiled 8^3 block, or a voxel of a
 //            leaf.  Outside every cascade box the region is a half-space the
 //            ray is leaving towards, or everything when it never comes back.
-//   cross    the first later lattice point outside the region is found by a
-//            galloping then bisecting search over k.  Every probe evaluates
-//            the point exactly as the definition does.
+//   cross    the first later lattice point outside the region.  The ray's
+//            parameter at the region's exit plane gives an estimate through
+//            a bucket index over the lattice; two exact probes confirm it
+//            (a gallop and bisection take over when they do not).  Every
+//            probe evaluates the point exactly as the definition does.
 //
 // Why this is exact: binary32 rounding is monotone, so for a fixed ray each
 // coordinate fl(o + fl(tm_k * d)) is monotone in k, and so is every voxel
@@ -27,9 +29,18 @@
 // The result is the sample set of the definition, with dense DDA and HDDA
 // bit-identical; HDDA just crosses far fewer regions.
 //
-// Output is produced in two passes (count, then emit) with the per-CTA
-// totals scanned by the last CTA of the count pass, so emission needs no
-// separate scan kernel and rays with no samples are not walked twice.
+// Launch shapes.  The allocating entry points run two kernels: walk_kernel
+// (persistent warps take 32-ray tiles in order from an atomic counter and
+// walk them with the lattice, bucket, threshold and node tables staged in
+// shared memory; each ray's sample count and merged occupied runs go to
+// global memory, with no CTA barrier anywhere) and emit_kernel (each CTA
+// loads 128 counts, publishes their sum at once and finds its output offset
+// by a decoupled look-back over earlier tiles, writes the CSR offsets, and
+// every warp expands its rays' runs into (ray, t_k, t_k+1) samples with
+// coalesced stores).  The allocation-free entry point runs one kernel,
+// onepass_kernel, whose CTAs keep the runs in shared memory and look back
+// right after walking, so its scratch stays a few hundred kilobytes.  A ray
+// with more runs than are kept walks again and writes its own samples.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -40,8 +51,18 @@
 namespace hdda {
 namespace {
 
-constexpr int kBS = 128;  // threads per CTA of the samplers
+constexpr int kBS = 128;        // rays (threads) per CTA tile
+constexpr int kMaxRuns = 16;    // runs per ray kept in shared memory
 constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kSpinLimit = 1u << 22;  // look-back polls before giving up
+
+// Loads from a table that lives in shared memory (kSm) or in global memory
+// (read-only path).
+template <bool kSm, typename T>
+__device__ __forceinline__ T ld(const T* p) {
+  if constexpr (kSm) return *p;
+  else return __ldg(p);
+}
 
 // ---------------------------------------------------------------------------
 // lattice
@@ -66,8 +87,13 @@ __global__ void lattice_count_kernel(hdda_params p, int64_t* out) {
   out[1] = limit;
 }
 
-__global__ void lattice_fill_kernel(hdda_params p, int K, float* __restrict__ t_out,
-                                    float* __restrict__ tm_out) {
+// Fills t, tm and the bucket index of a lattice block laid out as
+// lattice_block_bytes(max_k): t[max_k+1], tm[max_k], kidx[kKidxMax+2], hdr[4].
+__global__ void lattice_fill_kernel(hdda_params p, int K, int max_k, char* __restrict__ block) {
+  float* t_out = reinterpret_cast<float*>(block);
+  float* tm_out = t_out + max_k + 1;
+  int* kidx = reinterpret_cast<int*>(tm_out + max_k);
+  uint32_t* hdr = reinterpret_cast<uint32_t*>(kidx + kKidxMax + 2);
   float t = p.near_t;
   t_out[0] = t;
   for (int k = 0; k < K; ++k) {
@@ -76,6 +102,50 @@ __global__ void lattice_fill_kernel(hdda_params p, int K, float* __restrict__ t_
     tm_out[k] = __fmul_rn(__fadd_rn(t, tn), 0.5f);
     t = tn;
   }
+  if (K == 0) {
+    kidx[0] = kidx[1] = 0;
+    hdr[0] = hdr[1] = hdr[2] = 0;
+    return;
+  }
+  const uint32_t key0 = float_key(tm_out[0]);
+  const uint32_t range = float_key(tm_out[K - 1]) - key0;
+  uint32_t shift = 0;
+  while ((range >> shift) >= (uint32_t)kKidxMax) ++shift;
+  const int NB = (int)(range >> shift) + 1;
+  int k = 0;
+  for (int b = 0; b <= NB; ++b) {
+    const uint64_t bound = (uint64_t)key0 + ((uint64_t)b << shift);
+    while (k < K && (uint64_t)float_key(tm_out[k]) < bound) ++k;
+    kidx[b] = k;
+  }
+  kidx[NB + 1] = K;
+  hdr[0] = key0;
+  hdr[1] = shift;
+  hdr[2] = (uint32_t)NB;
+}
+
+LatticeDev lattice_view(char* block, int max_k, int K) {
+  float* t = reinterpret_cast<float*>(block);
+  float* tm = t + max_k + 1;
+  int* kidx = reinterpret_cast<int*>(tm + max_k);
+  uint32_t* hdr = reinterpret_cast<uint32_t*>(kidx + kKidxMax + 2);
+  return LatticeDev{t, tm, kidx, hdr, K};
+}
+
+struct LatHdr {
+  uint32_t key0, shift;
+  int NB;
+};
+
+// First k with tm_k >= te (K if none), through the bucket index.
+template <bool kSm>
+__device__ __forceinline__ int first_k_at(const LatticeDev& lat, const LatHdr& h, float te) {
+  const uint32_t key = float_key(te);
+  const int b = key < h.key0 ? 0 : (int)min((key - h.key0) >> h.shift, (uint32_t)h.NB);
+  int lo = ld<kSm>(lat.kidx + b);
+  const int hi = ld<kSm>(lat.kidx + b + 1);
+  while (lo < hi && ld<kSm>(lat.tm + lo) < te) ++lo;
+  return lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -83,7 +153,7 @@ __global__ void lattice_fill_kernel(hdda_params p, int K, float* __restrict__ t_
 // ---------------------------------------------------------------------------
 
 struct Ray {
-  float o[3], d[3];
+  float o[3], d[3], inv[3];
   bool neg[3];  // direction component < 0 (a zero component counts as positive)
 };
 
@@ -96,8 +166,23 @@ __device__ __forceinline__ bool load_ray(const float* __restrict__ ro,
     ray.d[c] = __ldg(rd + 3 * r + c);
     ok &= isfinite(ray.o[c]) && isfinite(ray.d[c]);
     ray.neg[c] = ray.d[c] < 0.f;
+    ray.inv[c] = 1.0f / ray.d[c];  // estimates only
   }
   return ok;
+}
+
+// The grid tables the walk reads per region, in shared memory (staged) or
+// global memory; the rest of the grid stays in the GridDev kernel parameter.
+struct Tabs {
+  const float* thr;
+  const uint32_t* child;
+  const uint32_t* tile;
+  const uint32_t* prefix;
+  const uint32_t* nstate;
+};
+
+__device__ __forceinline__ Tabs global_tabs(const GridDev& g) {
+  return Tabs{g.thr, g.child, g.tile, g.prefix, g.nstate};
 }
 
 // x = o + tm * d per axis, one rounding per operation.
@@ -121,16 +206,18 @@ __device__ __forceinline__ void clip(float e[3], const Ray& r, int c, float lo, 
 
 // Intersects the region with voxels [a0, a1) of axis c of one level, using
 // the exact thresholds X[a] (only the bound on the exit side is loaded).
-__device__ __forceinline__ void clip_cells(float e[3], const Ray& r, const float* __restrict__ thr,
-                                           int R1, int c, int a0, int a1) {
-  if (r.neg[c]) e[c] = fmaxf(e[c], __ldg(thr + c * R1 + a0));
-  else e[c] = fminf(e[c], __ldg(thr + c * R1 + a1));
+template <bool kSm>
+__device__ __forceinline__ void clip_cells(float e[3], const Ray& r, const float* thr, int R1,
+                                           int c, int a0, int a1) {
+  if (r.neg[c]) e[c] = fmaxf(e[c], ld<kSm>(thr + c * R1 + a0));
+  else e[c] = fminf(e[c], ld<kSm>(thr + c * R1 + a1));
 }
 
 // Classifies x and sets e to the region holding it.  Returns its occupancy.
-template <bool kVdb>
-__device__ __forceinline__ bool locate(const GridDev& g, const Ray& r, const float x[3],
-                                       float e[3]) {
+// kSm: thresholds and node arrays of g point into shared memory.
+template <bool kVdb, bool kSm>
+__device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const Ray& r,
+                                       const float x[3], float e[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) e[c] = r.neg[c] ? -INFINITY : INFINITY;
   int l = -1;
@@ -150,13 +237,13 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Ray& r, const flo
       if (x[c] < B.lo[c]) {
         if (!(r.d[c] > 0.f)) never = true;  // coordinate never grows: never enters
         else {
-          const float t = __fdividef(B.lo[c] - x[c], r.d[c]);
+          const float t = (B.lo[c] - x[c]) * r.inv[c];
           if (t > best_t) { best_t = t; best = c; }
         }
       } else if (x[c] >= B.hi[c]) {
         if (!(r.d[c] < 0.f)) never = true;
         else {
-          const float t = __fdividef(x[c] - B.hi[c], -r.d[c]);
+          const float t = (B.hi[c] - x[c]) * r.inv[c];
           if (t > best_t) { best_t = t; best = c; }
         }
       }
@@ -179,24 +266,24 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Ray& r, const flo
     i[c] = voxel_index(x[c], V.lo[c], V.s[c], g.R);
   }
   const int R1 = g.R + 1;
-  const float* thr = g.thr + (int64_t)l * 3 * R1;
+  const float* thr = tb.thr + (int64_t)l * 3 * R1;
   if (!kVdb) {
     const int64_t lin = ((int64_t)i[0] * g.R + i[1]) * g.R + i[2];
     const uint32_t w = __ldg(g.bits + (int64_t)l * g.W + (lin >> 5));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) clip_cells(e, r, thr, R1, c, i[c], i[c] + 1);
+    for (int c = 0; c < 3; ++c) clip_cells<kSm>(e, r, thr, R1, c, i[c], i[c] + 1);
     return (w >> (lin & 31)) & 1u;
   }
   // node level
   const int N = g.N;
   const int64_t ng = (int64_t)l * N * N * N +
                      ((i[0] >> 7) * N + (i[1] >> 7)) * N + (i[2] >> 7);
-  const uint32_t st = __ldg(g.nstate + ng);
+  const uint32_t st = ld<kSm>(tb.nstate + ng);
   if (st != kNodeMixed) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int a0 = i[c] & ~(kNodeVox - 1);
-      clip_cells(e, r, thr, R1, c, a0, min(a0 + kNodeVox, g.R));
+      clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + kNodeVox, g.R));
     }
     return st == kNodeFull;
   }
@@ -204,49 +291,79 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Ray& r, const flo
   const int cell = (((i[0] >> 3) & 15) * 16 + ((i[1] >> 3) & 15)) * 16 + ((i[2] >> 3) & 15);
   const int w = cell >> 5;
   const uint32_t bit = 1u << (cell & 31);
-  const uint32_t cw = __ldg(g.child + ng * kNodeWords + w);
+  const uint32_t cw = ld<kSm>(tb.child + ng * kNodeWords + w);
   if (!(cw & bit)) {
-    const uint32_t tw = __ldg(g.tile + ng * kNodeWords + w);
+    const uint32_t tw = ld<kSm>(tb.tile + ng * kNodeWords + w);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int a0 = i[c] & ~(kBlockDim - 1);
-      clip_cells(e, r, thr, R1, c, a0, min(a0 + kBlockDim, g.R));
+      clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + kBlockDim, g.R));
     }
     return (tw & bit) != 0u;
   }
   // voxel of a leaf
-  const uint32_t leaf = __ldg(g.prefix + ng * kNodeWords + w) + __popc(cw & (bit - 1u));
+  const uint32_t leaf = ld<kSm>(tb.prefix + ng * kNodeWords + w) + __popc(cw & (bit - 1u));
   const int v = ((i[0] & 7) * 8 + (i[1] & 7)) * 8 + (i[2] & 7);
   const uint32_t lw = __ldg(g.leaves + (int64_t)leaf * kLeafWords + (v >> 5));
 #pragma unroll
-  for (int c = 0; c < 3; ++c) clip_cells(e, r, thr, R1, c, i[c], i[c] + 1);
+  for (int c = 0; c < 3; ++c) clip_cells<kSm>(e, r, thr, R1, c, i[c], i[c] + 1);
   return (lw >> (v & 31)) & 1u;
 }
 
 // First k' in (k, K] whose point is outside the region (K if none).  The
 // point of k is inside.  xo receives the point of k' when k' < K.
-__device__ __forceinline__ int cross(const Ray& r, const float* __restrict__ tm, int k, int K,
+template <bool kSm>
+__device__ __forceinline__ int cross(const Ray& r, const LatticeDev& lat, const LatHdr& h, int k,
                                      const float e[3], float xo[3]) {
-  int lo = k, hi, step = 1;
-  for (;;) {
-    hi = lo + step;
-    if (hi >= K) { hi = K; break; }
-    float xh[3];
-    point_at(r, __ldg(tm + hi), xh);
-    if (outside(xh, e, r)) {
-      xo[0] = xh[0]; xo[1] = xh[1]; xo[2] = xh[2];
-      break;
+  const int K = lat.K;
+  // estimate: the ray parameter where it meets the first exit plane
+  float te = INFINITY;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    if (r.d[c] != 0.f) te = fminf(te, (e[c] - r.o[c]) * r.inv[c]);
+  int ke = max(first_k_at<kSm>(lat, h, te), k + 1);
+  int lo, hi;  // invariant: point lo inside (lo >= k); point hi outside, or hi == K
+  float xp[3];
+  if (ke >= K) {
+    if (K - 1 == k) return K;
+    point_at(r, ld<kSm>(lat.tm + K - 1), xp);
+    if (!outside(xp, e, r)) return K;
+    lo = k;
+    hi = K - 1;
+    xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
+  } else {
+    point_at(r, ld<kSm>(lat.tm + ke), xp);
+    if (!outside(xp, e, r)) {
+      // estimate too early: gallop forward
+      lo = ke;
+      int step = 1;
+      for (;;) {
+        hi = lo + step;
+        if (hi >= K) { hi = K; break; }
+        point_at(r, ld<kSm>(lat.tm + hi), xp);
+        if (outside(xp, e, r)) {
+          xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
+          break;
+        }
+        lo = hi;
+        step <<= 1;
+      }
+    } else {
+      xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
+      if (ke - 1 == k) return ke;
+      point_at(r, ld<kSm>(lat.tm + ke - 1), xp);
+      if (!outside(xp, e, r)) return ke;  // the usual case: estimate exact
+      lo = k;
+      hi = ke - 1;
+      xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
     }
-    lo = hi;
-    step <<= 1;
   }
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    float xm[3];
-    point_at(r, __ldg(tm + mid), xm);
-    if (outside(xm, e, r)) {
+    point_at(r, ld<kSm>(lat.tm + mid), xp);
+    if (outside(xp, e, r)) {
       hi = mid;
-      xo[0] = xm[0]; xo[1] = xm[1]; xo[2] = xm[2];
+      xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
     } else {
       lo = mid;
     }
@@ -254,38 +371,63 @@ __device__ __forceinline__ int cross(const Ray& r, const float* __restrict__ tm,
   return hi;
 }
 
-template <bool kVdb, bool kEmit>
-__device__ __forceinline__ int64_t walk(const GridDev& g, const LatticeDev& lat, const Ray& r,
-                                        int32_t rid, int64_t out, int32_t* __restrict__ ray_idx,
-                                        float* __restrict__ t0, float* __restrict__ t1,
-                                        unsigned* __restrict__ status) {
+// Walks one ray.  Counts its samples and merges occupied regions into runs
+// [k_begin, k_end): the first kMaxRuns go to runs[j * stride]; nruns counts
+// all.  With kEmit it instead writes the samples from `out`, below
+// `capacity` (lat.t must then be a global-memory table).
+template <bool kVdb, bool kEmit, bool kSm>
+__device__ __forceinline__ int64_t walk(const GridDev& g, const Tabs& tb, const LatticeDev& lat,
+                                        const LatHdr& h, const Ray& r, uint2* runs,
+                                        int64_t stride, int& nruns, int32_t rid,
+                                        int64_t out, int64_t capacity,
+                                        int32_t* __restrict__ ray_idx, float* __restrict__ t0,
+                                        float* __restrict__ t1, unsigned* __restrict__ status) {
   const int K = lat.K;
   int64_t cnt = 0;
+  nruns = 0;
   if (K <= 0) return 0;
+  int rb = -1, re = -1;  // open run
   float x[3];
-  point_at(r, __ldg(lat.tm), x);
+  point_at(r, ld<kSm>(lat.tm), x);
   int k = 0;
   while (k < K) {
     float e[3];
-    const bool occ = locate<kVdb>(g, r, x, e);
+    const bool occ = locate<kVdb, kSm>(g, tb, r, x, e);
     if (outside(x, e, r)) atomicOr(status, kDevInternal);  // region must hold its point
-    const int kn = cross(r, lat.tm, k, K, e, x);
+    const int kn = cross<kSm>(r, lat, h, k, e, x);
     if (occ) {
       if (kEmit) {
         float ta = __ldg(lat.t + k);
         for (int j = k; j < kn; ++j) {
           const float tb = __ldg(lat.t + j + 1);
-          ray_idx[out + cnt] = rid;
-          t0[out + cnt] = ta;
-          t1[out + cnt] = tb;
+          const int64_t p = out + cnt;
+          if (p < capacity) {
+            ray_idx[p] = rid;
+            t0[p] = ta;
+            t1[p] = tb;
+          }
           ta = tb;
           ++cnt;
         }
       } else {
         cnt += kn - k;
+        if (k == re) {
+          re = kn;  // adjacent occupied region: extend the run
+        } else {
+          if (rb >= 0) {
+            if (nruns < kMaxRuns) runs[nruns * stride] = make_uint2(rb, re);
+            ++nruns;
+          }
+          rb = k;
+          re = kn;
+        }
       }
     }
     k = kn;
+  }
+  if (!kEmit && rb >= 0) {
+    if (nruns < kMaxRuns) runs[nruns * stride] = make_uint2(rb, re);
+    ++nruns;
   }
   return cnt;
 }
@@ -317,79 +459,319 @@ __device__ __forceinline__ int64_t cta_exclusive_scan64(int64_t v, int64_t* tota
   return res;
 }
 
-// Pass 1: per-ray counts into offsets[r]; per-CTA sums; the last CTA to
-// finish scans the CTA sums into tile_prefix and writes the total.
-template <bool kVdb>
-__global__ void __launch_bounds__(kBS) count_kernel(
-    const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
-    LatticeDev lat, int64_t* __restrict__ offsets, int64_t* __restrict__ tile_sum,
-    int64_t* __restrict__ tile_prefix, unsigned* __restrict__ ticket,
-    unsigned* __restrict__ status, int64_t* __restrict__ total) {
-  const int64_t r = blockIdx.x * (int64_t)kBS + threadIdx.x;
-  int64_t c = 0;
-  if (r < n) {
-    Ray ray;
-    if (load_ray(ro, rd, r, ray))
-      c = walk<kVdb, false>(g, lat, ray, (int32_t)r, 0, nullptr, nullptr, nullptr, status);
-    offsets[r] = c;
+// ---------------------------------------------------------------------------
+// decoupled look-back over tiles
+// ---------------------------------------------------------------------------
+
+constexpr unsigned long long kFlagAggregate = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Publishes this tile's aggregate, sums the predecessors back to the first
+// published prefix, publishes the inclusive prefix and returns the
+// exclusive one.  Called by one whole warp, which reads 32 predecessors per
+// poll.  Every predecessor tile was handed out earlier and is running or
+// done, so each wait ends; the poll count is still bounded, and running out
+// of it raises kDevTimeout (the host then reports HDDA_ERR_TIMEOUT) and
+// publishes what it has so that later tiles finish.
+__device__ int64_t lookback(unsigned long long* state, int tile, int64_t agg,
+                            unsigned* status) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_release(state, kFlagPrefix | (unsigned long long)agg);
+    return 0;
   }
-  int64_t bsum = 0;
-  cta_exclusive_scan64(c, &bsum);
-  __shared__ bool is_last;
-  if (threadIdx.x == 0) {
-    tile_sum[blockIdx.x] = bsum;
-    __threadfence();
-    is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (lane == 0) st_release(state + tile, kFlagAggregate | (unsigned long long)agg);
+  int64_t excl = 0;
+  int base = tile - 1;  // lane i looks at tile base - i
+  unsigned polls = 0;
+  for (;;) {
+    const int j = base - lane;
+    const unsigned long long w = j >= 0 ? ld_acquire(state + j) : kFlagPrefix;
+    const unsigned long long f = w & ~kValueMask;
+    const unsigned pmask = __ballot_sync(kFull, f == kFlagPrefix);
+    const unsigned zmask = __ballot_sync(kFull, f == 0);
+    const int first_p = pmask ? __ffs(pmask) - 1 : 32;  // nearest published prefix
+    const unsigned need = first_p >= 31 ? kFull : ((2u << first_p) - 1u);
+    if (zmask & need) {  // a tile this one depends on has not published yet
+      if (++polls > kSpinLimit) {
+        if (lane == 0) atomicOr(status, kDevTimeout);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    int64_t v = lane <= first_p ? (int64_t)(w & kValueMask) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    excl += v;
+    if (first_p < 32) break;
+    base -= 32;
+  }
+  if (lane == 0) st_release(state + tile, kFlagPrefix | (unsigned long long)(excl + agg));
+  return excl;
+}
+
+// ---------------------------------------------------------------------------
+// expansion of runs into samples
+// ---------------------------------------------------------------------------
+
+// One warp writes the samples of its 32 rays.  Lane i holds ray rid0 + i
+// with `c` samples from output position `off` (rays in order, so the
+// warp's samples are one contiguous range); its runs are runs0[i + j *
+// stride], j < kMaxRuns.  Lane j of each 32-sample chunk finds the ray that
+// owns its position (binary search over the lanes' offsets) and the run
+// inside it.  Rays with more runs than were kept are skipped here; they
+// walk again.  Nothing at or past `capacity` is written.
+template <bool kSm>
+__device__ __forceinline__ void expand_warp(int64_t off, int64_t c, bool overflow,
+                                            const uint2* runs0, int64_t stride, int32_t rid0,
+                                            const float* __restrict__ t, int64_t capacity,
+                                            int32_t* __restrict__ ray_idx,
+                                            float* __restrict__ t0, float* __restrict__ t1) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wbeg = __shfl_sync(kFull, off, 0);
+  const int64_t wend = __shfl_sync(kFull, off + c, 31);
+  for (int64_t base = wbeg; base < wend; base += 32) {
+    const int64_t p = base + lane;
+    int own = 0;  // the last lane whose offset is <= p
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      const int64_t v = __shfl_sync(kFull, off, own + s);
+      if (v <= p) own += s;
+    }
+    const int64_t own_off = __shfl_sync(kFull, off, own);
+    const int own_ovf = __shfl_sync(kFull, (int)overflow, own);
+    if (p < wend && !own_ovf && p < capacity) {
+      const uint2* rr = runs0 + own;
+      int64_t loc = p - own_off;
+      uint2 run = ld<kSm>(rr);
+      int j = 0;
+      while (loc >= (int64_t)(run.y - run.x)) {
+        loc -= run.y - run.x;
+        run = ld<kSm>(rr + (++j) * stride);
+      }
+      const int k = (int)run.x + (int)loc;
+      ray_idx[p] = rid0 + own;
+      t0[p] = __ldg(t + k);
+      t1[p] = __ldg(t + k + 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one-pass sampler (bounded scratch: runs stay in shared memory)
+// ---------------------------------------------------------------------------
+
+template <bool kVdb>
+__global__ void __launch_bounds__(kBS) onepass_kernel(
+    const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
+    LatticeDev lat, int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx,
+    float* __restrict__ t0, float* __restrict__ t1, int64_t capacity,
+    unsigned long long* __restrict__ tile_state, unsigned* __restrict__ tile_counter,
+    unsigned* __restrict__ status, int64_t* __restrict__ total_out) {
+  __shared__ uint2 s_runs[kMaxRuns * kBS];
+  __shared__ int s_tile;
+  __shared__ int64_t s_prefix;
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const int tile = s_tile;
+  const int64_t r = (int64_t)tile * kBS + threadIdx.x;
+  const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+
+  Ray ray;
+  bool valid = false;
+  int64_t c = 0;
+  int nruns = 0;
+  if (r < n) {
+    valid = load_ray(ro, rd, r, ray);
+    if (valid)
+      c = walk<kVdb, false, false>(g, global_tabs(g), lat, h, ray, s_runs + threadIdx.x, kBS,
+                                   nruns, 0, 0, 0, nullptr, nullptr, nullptr, status);
+  }
+  int64_t agg = 0;
+  const int64_t local = cta_exclusive_scan64(c, &agg);
+  if (threadIdx.x < 32) {
+    const int64_t pre = lookback(tile_state, tile, agg, status);
+    if (threadIdx.x == 0) s_prefix = pre;
   }
   __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  int64_t carry = 0;
-  for (int64_t c0 = 0; c0 < gridDim.x; c0 += kBS) {
-    const int64_t i = c0 + threadIdx.x;
-    const int64_t v = i < gridDim.x ? __ldcg(tile_sum + i) : 0;
-    int64_t chunk = 0;
-    const int64_t ex = cta_exclusive_scan64(v, &chunk);
-    if (i < gridDim.x) tile_prefix[i] = carry + ex;
-    carry += chunk;
-  }
-  if (threadIdx.x == 0) *total = carry;
-}
-
-// Turns the counts in offsets[] into CSR row pointers.
-__device__ __forceinline__ int64_t finish_offsets(int64_t r, int64_t n, int64_t* offsets,
-                                                  const int64_t* tile_prefix,
-                                                  const int64_t* total, int64_t& c) {
-  c = r < n ? offsets[r] : 0;
-  int64_t unused = 0;
-  const int64_t off = __ldg(tile_prefix + blockIdx.x) + cta_exclusive_scan64(c, &unused);
+  const int64_t off = s_prefix + local;
   if (r < n) offsets[r] = off;
-  if (blockIdx.x == 0 && threadIdx.x == 0) offsets[n] = *total;
-  return off;
+  if (tile == (int)gridDim.x - 1 && threadIdx.x == kBS - 1) {
+    offsets[n] = off + c;
+    *total_out = off + c;
+  }
+  if (capacity <= 0) return;
+  const int warp = threadIdx.x >> 5;
+  const bool overflow = nruns > kMaxRuns;
+  expand_warp<true>(off, c, overflow, s_runs + warp * 32, kBS,
+                    (int32_t)((int64_t)tile * kBS + warp * 32), lat.t, capacity, ray_idx, t0, t1);
+  if (overflow && valid) {
+    int unused = 0;
+    walk<kVdb, true, false>(g, global_tabs(g), lat, h, ray, nullptr, 0, unused, (int32_t)r, off,
+                            capacity, ray_idx, t0, t1, status);
+  }
 }
 
-__global__ void __launch_bounds__(kBS) offsets_kernel(int64_t n, int64_t* __restrict__ offsets,
-                                                      const int64_t* __restrict__ tile_prefix,
-                                                      const int64_t* __restrict__ total) {
-  const int64_t r = blockIdx.x * (int64_t)kBS + threadIdx.x;
-  int64_t c;
-  finish_offsets(r, n, offsets, tile_prefix, total, c);
+// ---------------------------------------------------------------------------
+// two-pass sampler: walk (persistent warps, staged tables), then emit
+// ---------------------------------------------------------------------------
+
+constexpr int kWalkBS = 256;
+
+// Shared-memory bytes that stage the walk's tables (0 = they do not fit).
+struct StageLayout {
+  size_t tm, kidx, thr, child, tile, prefix, nstate, bytes;
+};
+
+__host__ __device__ inline StageLayout stage_layout(int K, int L, int R, int64_t nodes, bool vdb) {
+  StageLayout s{};
+  size_t o = 0;
+  s.tm = o; o += sizeof(float) * (size_t)K;
+  s.kidx = o; o += sizeof(int) * (size_t)(kKidxMax + 2);
+  s.thr = o; o += sizeof(float) * (size_t)L * 3 * (R + 1);
+  s.child = s.tile = s.prefix = s.nstate = o;
+  if (vdb) {
+    s.child = o; o += 4 * (size_t)nodes * kNodeWords;
+    s.tile = o; o += 4 * (size_t)nodes * kNodeWords;
+    s.prefix = o; o += 4 * (size_t)nodes * kNodeWords;
+    s.nstate = o; o += 4 * (size_t)nodes;
+  }
+  s.bytes = (o + 15) & ~(size_t)15;
+  return s;
 }
 
-// Pass 2: row pointers, then every ray with samples walks again and writes them.
+constexpr size_t kMaxStageBytes = 96 * 1024;
+
+template <typename T>
+__device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, int64_t count) {
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+// Pass 1.  Persistent: each warp takes 32-ray tiles in order until none is
+// left, so a warp never waits for another.  Writes counts[r], nruns[r]
+// (saturated at 255) and the first kMaxRuns runs at runs[r + j * n].
+template <bool kVdb, bool kSm>
+__global__ void __launch_bounds__(kWalkBS) walk_kernel(
+    const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
+    LatticeDev lat, int32_t* __restrict__ counts, uint8_t* __restrict__ nruns_out,
+    uint2* __restrict__ runs, unsigned* __restrict__ tile_counter,
+    unsigned* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+  Tabs tb = global_tabs(g);
+  LatticeDev ls = lat;
+  if constexpr (kSm) {
+    const int64_t nodes = (int64_t)g.L * g.N * g.N * g.N;
+    const StageLayout sl = stage_layout(lat.K, g.L, g.R, nodes, kVdb);
+    float* s_tm = reinterpret_cast<float*>(smem + sl.tm);
+    int* s_kidx = reinterpret_cast<int*>(smem + sl.kidx);
+    float* s_thr = reinterpret_cast<float*>(smem + sl.thr);
+    stage_copy(s_tm, lat.tm, lat.K);
+    stage_copy(s_kidx, lat.kidx, (int64_t)h.NB + 2);
+    stage_copy(s_thr, g.thr, (int64_t)g.L * 3 * (g.R + 1));
+    ls.tm = s_tm;
+    ls.kidx = s_kidx;
+    tb.thr = s_thr;
+    if constexpr (kVdb) {
+      uint32_t* s_child = reinterpret_cast<uint32_t*>(smem + sl.child);
+      uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + sl.tile);
+      uint32_t* s_prefix = reinterpret_cast<uint32_t*>(smem + sl.prefix);
+      uint32_t* s_nstate = reinterpret_cast<uint32_t*>(smem + sl.nstate);
+      stage_copy(s_child, g.child, nodes * kNodeWords);
+      stage_copy(s_tile, g.tile, nodes * kNodeWords);
+      stage_copy(s_prefix, g.prefix, nodes * kNodeWords);
+      stage_copy(s_nstate, g.nstate, nodes);
+      tb.child = s_child;
+      tb.tile = s_tile;
+      tb.prefix = s_prefix;
+      tb.nstate = s_nstate;
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const unsigned ntiles = (unsigned)((n + 31) / 32);
+  for (;;) {
+    unsigned tile = 0;
+    if (lane == 0) tile = atomicAdd(tile_counter, 1u);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= ntiles) break;
+    const int64_t r = (int64_t)tile * 32 + lane;
+    if (r < n) {
+      Ray ray;
+      int nr = 0;
+      int64_t c = 0;
+      if (load_ray(ro, rd, r, ray))
+        c = walk<kVdb, false, kSm>(g, tb, ls, h, ray, runs + r, n, nr, 0, 0, 0, nullptr, nullptr,
+                                   nullptr, status);
+      counts[r] = (int32_t)c;
+      nruns_out[r] = (uint8_t)min(nr, 255);
+    }
+  }
+}
+
+// Pass 2.  Each CTA loads 128 counts, publishes their sum immediately, looks
+// back for its offset, writes the CSR offsets and expands the runs.
 template <bool kVdb>
 __global__ void __launch_bounds__(kBS) emit_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
-    LatticeDev lat, int64_t* __restrict__ offsets, const int64_t* __restrict__ tile_prefix,
-    const int64_t* __restrict__ total, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
-    float* __restrict__ t1, unsigned* __restrict__ status) {
-  const int64_t r = blockIdx.x * (int64_t)kBS + threadIdx.x;
-  int64_t c;
-  const int64_t off = finish_offsets(r, n, offsets, tile_prefix, total, c);
-  if (r < n && c > 0) {
+    LatticeDev lat, const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
+    const uint2* __restrict__ runs, int64_t* __restrict__ offsets,
+    int32_t* __restrict__ ray_idx, float* __restrict__ t0, float* __restrict__ t1,
+    int64_t capacity, unsigned long long* __restrict__ tile_state,
+    unsigned* __restrict__ tile_counter, unsigned* __restrict__ status,
+    int64_t* __restrict__ total_out) {
+  __shared__ uint2 s_runs[kMaxRuns * kBS];  // run j of the CTA's ray i at [j * kBS + i]
+  __shared__ int s_tile;
+  __shared__ int64_t s_prefix;
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const int tile = s_tile;
+  const int64_t r = (int64_t)tile * kBS + threadIdx.x;
+  const int64_t c = r < n ? (int64_t)counts[r] : 0;
+  const int nr = r < n ? (int)nruns[r] : 0;
+  if (capacity > 0) {  // runs to shared memory first (their loads overlap the look-back)
+    const int kept = min(nr, kMaxRuns);
+    for (int j = 0; __any_sync(kFull, j < kept); ++j)
+      if (j < kept) s_runs[j * kBS + threadIdx.x] = __ldg(runs + (int64_t)j * n + r);
+  }
+  int64_t agg = 0;
+  const int64_t local = cta_exclusive_scan64(c, &agg);
+  if (threadIdx.x < 32) {
+    const int64_t pre = lookback(tile_state, tile, agg, status);
+    if (threadIdx.x == 0) s_prefix = pre;
+  }
+  __syncthreads();
+  const int64_t off = s_prefix + local;
+  if (r < n) offsets[r] = off;
+  if (tile == (int)gridDim.x - 1 && threadIdx.x == kBS - 1) {
+    offsets[n] = off + c;
+    *total_out = off + c;
+  }
+  if (capacity <= 0) return;
+  const int warp = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)tile * kBS + warp * 32;
+  const bool overflow = nr > kMaxRuns;
+  expand_warp<true>(off, c, overflow, s_runs + warp * 32, kBS, (int32_t)r0, lat.t, capacity,
+                    ray_idx, t0, t1);
+  if (overflow) {
     Ray ray;
     load_ray(ro, rd, r, ray);
-    walk<kVdb, true>(g, lat, ray, (int32_t)r, off, ray_idx, t0, t1, status);
+    const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+    int unused = 0;
+    walk<kVdb, true, false>(g, global_tabs(g), lat, h, ray, nullptr, 0, unused, (int32_t)r, off,
+                            capacity, ray_idx, t0, t1, status);
   }
 }
 
@@ -400,8 +782,7 @@ __global__ void __launch_bounds__(kBS) emit_kernel(
 struct LatticeEntry {
   hdda_params key;
   int device;
-  float* t;
-  float* tm;
+  char* block;
   int K;
   int status;
 };
@@ -425,7 +806,15 @@ int validate_params(const hdda_params* p) {
   return HDDA_OK;
 }
 
-// Pinned host words for the one read-back per call.
+hdda_params canonical(const hdda_params& p) {
+  hdda_params key;
+  std::memset(&key, 0, sizeof(key));
+  key.near_t = p.near_t; key.far_t = p.far_t; key.step = p.step;
+  key.cone_angle = p.cone_angle; key.max_step = p.max_step; key.max_steps = p.max_steps;
+  return key;
+}
+
+// Pinned host words for the read-backs of the allocating path.
 struct HostWords {
   int64_t* p = nullptr;
   ~HostWords() { if (p) cudaFreeHost(p); }
@@ -444,16 +833,13 @@ int host_words(int64_t** out) {
 int get_lattice(const hdda_params& p, cudaStream_t s, LatticeDev* out) {
   int dev = 0;
   HDDA_CUDA_TRY(cudaGetDevice(&dev));
-  hdda_params key;
-  std::memset(&key, 0, sizeof(key));
-  key.near_t = p.near_t; key.far_t = p.far_t; key.step = p.step;
-  key.cone_angle = p.cone_angle; key.max_step = p.max_step; key.max_steps = p.max_steps;
+  const hdda_params key = canonical(p);
   std::lock_guard<std::mutex> lock(g_lattice_mu);
   for (const LatticeEntry& e : g_lattices) {
     if (e.device == dev && same_params(e.key, key)) {
       if (e.status != HDDA_OK)
         return set_error(e.status, "lattice has more than max_steps=%d candidates", p.max_steps);
-      *out = LatticeDev{e.t, e.tm, e.K};
+      *out = lattice_view(e.block, e.K, e.K);
       return HDDA_OK;
     }
   }
@@ -467,29 +853,25 @@ int get_lattice(const hdda_params& p, cudaStream_t s, LatticeDev* out) {
   HDDA_CUDA_TRY(cudaMemcpyAsync(hw, dk, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   HDDA_CUDA_TRY(cudaFreeAsync(dk, s));
   HDDA_CUDA_TRY(cudaStreamSynchronize(s));
-  LatticeEntry e{key, dev, nullptr, nullptr, (int)hw[0], HDDA_OK};
+  LatticeEntry e{key, dev, nullptr, (int)hw[0], HDDA_OK};
   if (hw[1]) {
     e.status = HDDA_ERR_STEP_LIMIT;
     g_lattices.push_back(e);
     return set_error(HDDA_ERR_STEP_LIMIT, "lattice has more than max_steps=%d candidates",
                      p.max_steps);
   }
-  float* buf = nullptr;
-  HDDA_CUDA_TRY(cudaMalloc(&buf, sizeof(float) * (2 * (size_t)e.K + 1)));
-  e.t = buf;
-  e.tm = buf + e.K + 1;
-  lattice_fill_kernel<<<1, 1, 0, s>>>(key, e.K, e.t, e.tm);
+  HDDA_CUDA_TRY(cudaMalloc(&e.block, lattice_block_bytes(e.K)));
+  lattice_fill_kernel<<<1, 1, 0, s>>>(key, e.K, e.K, e.block);
   HDDA_CUDA_TRY(cudaGetLastError());
   HDDA_CUDA_TRY(cudaStreamSynchronize(s));  // published to every stream from here on
   g_lattices.push_back(e);
-  *out = LatticeDev{e.t, e.tm, e.K};
+  *out = lattice_view(e.block, e.K, e.K);
   return HDDA_OK;
 }
 
-int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
-             const hdda_params* params, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
-             int64_t capacity, int64_t* total_out, cudaStream_t s) {
-  clear_error();
+int check_args(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+               const hdda_params* params, int64_t* offsets, int32_t* ray_idx, float* t0,
+               float* t1, int64_t capacity, int64_t* total_out) {
   if (!grid) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
   if (grid->kind != (vdb ? HDDA_GRID_VDB : HDDA_GRID_DENSE))
     return set_error(HDDA_ERR_INVALID_ARG, vdb ? "hdda traversal needs a VDB grid"
@@ -507,6 +889,140 @@ int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_g
   if (dev != grid->device)
     return set_error(HDDA_ERR_INVALID_ARG, "grid lives on device %d, current is %d",
                      grid->device, dev);
+  return HDDA_OK;
+}
+
+// Reads the header words {.., status, total} back and turns them into a status.
+int finish(int64_t* hw, const char* header, int64_t capacity, int64_t* total_out,
+           cudaStream_t s) {
+  HDDA_CUDA_TRY(cudaMemcpyAsync(hw, header, 16, cudaMemcpyDeviceToHost, s));
+  HDDA_CUDA_TRY(cudaStreamSynchronize(s));
+  const unsigned dev_status = reinterpret_cast<unsigned*>(hw)[1];
+  const int64_t tot = hw[1];
+  *total_out = tot;
+  if (dev_status & kDevInternal)
+    return set_error(HDDA_ERR_INTERNAL, "region check failed on the device");
+  if (dev_status & kDevTimeout)
+    return set_error(HDDA_ERR_TIMEOUT, "tile look-back gave up waiting");
+  if (capacity > 0 && capacity < tot)
+    return set_error(HDDA_ERR_CAPACITY, "capacity %lld < %lld samples", (long long)capacity,
+                     (long long)tot);
+  return HDDA_OK;
+}
+
+// One-pass launch over scratch = [32-byte header | tile states]:
+// header = {tile counter u32, status u32, total i64}.
+int run_onepass(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+                const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
+                int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
+                cudaStream_t s) {
+  const unsigned nb = (unsigned)((n + kBS - 1) / kBS);
+  unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+  unsigned* status = counter + 1;
+  int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
+  unsigned long long* state = reinterpret_cast<unsigned long long*>(scratch + 32);
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 32 + 8 * (size_t)nb, s));
+  const GridDev g = grid->view();
+  if (vdb)
+    onepass_kernel<true><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0, t1,
+                                            capacity, state, counter, status, total);
+  else
+    onepass_kernel<false><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0, t1,
+                                             capacity, state, counter, status, total);
+  HDDA_CUDA_TRY(cudaGetLastError());
+  return finish(hw, scratch, capacity, total_out, s);
+}
+
+// Bytes of the two-pass scratch for n rays.
+size_t twopass_scratch_bytes(int64_t n) {
+  const int64_t nb = (n + kBS - 1) / kBS;
+  auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return 256 + a(8 * (size_t)nb) + a(4 * (size_t)n) + a((size_t)n) +
+         a(sizeof(uint2) * kMaxRuns * (size_t)n);
+}
+
+template <bool kVdb, bool kSm>
+int launch_walk(const float* ro, const float* rd, int64_t n, const GridDev& g,
+                const LatticeDev& lat, size_t smem, int32_t* counts, uint8_t* nruns, uint2* runs,
+                unsigned* counter, unsigned* status, cudaStream_t s) {
+  auto kern = walk_kernel<kVdb, kSm>;
+  if (smem > 48 * 1024)
+    HDDA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  HDDA_CUDA_TRY(cudaGetDevice(&dev));
+  HDDA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HDDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkBS, smem));
+  const int64_t want = (n + kWalkBS - 1) / kWalkBS;
+  const int64_t full = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  const unsigned grid = (unsigned)(want < full ? want : full);
+  kern<<<grid, kWalkBS, smem, s>>>(ro, rd, n, g, lat, counts, nruns, runs, counter, status);
+  HDDA_CUDA_TRY(cudaGetLastError());
+  return HDDA_OK;
+}
+
+// Two-pass launch.  Scratch: [0, 256) header {walk counter u32, status u32,
+// total i64, emit counter u32}, then tile states, counts, run counts, runs.
+int run_twopass(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+                const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
+                int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
+                cudaStream_t s) {
+  const int64_t nb = (n + kBS - 1) / kBS;
+  auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  unsigned* walk_counter = reinterpret_cast<unsigned*>(scratch);
+  unsigned* status = walk_counter + 1;
+  int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
+  unsigned* emit_counter = reinterpret_cast<unsigned*>(scratch + 16);
+  char* p = scratch + 256;
+  unsigned long long* state = reinterpret_cast<unsigned long long*>(p);
+  p += a(8 * (size_t)nb);
+  int32_t* counts = reinterpret_cast<int32_t*>(p);
+  p += a(4 * (size_t)n);
+  uint8_t* nruns = reinterpret_cast<uint8_t*>(p);
+  p += a((size_t)n);
+  uint2* runs = reinterpret_cast<uint2*>(p);
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256 + 8 * (size_t)nb, s));
+
+  const GridDev g = grid->view();
+  const StageLayout sl = stage_layout(lat.K, g.L, g.R, grid->nodes_total(), vdb);
+  const bool staged = sl.bytes <= kMaxStageBytes;
+  {
+    KernelTimer kt(vdb ? "hdda_walk" : "dense_walk", s);
+    int st;
+    if (vdb)
+      st = staged ? launch_walk<true, true>(ro, rd, n, g, lat, sl.bytes, counts, nruns, runs,
+                                            walk_counter, status, s)
+                  : launch_walk<true, false>(ro, rd, n, g, lat, 0, counts, nruns, runs,
+                                             walk_counter, status, s);
+    else
+      st = staged ? launch_walk<false, true>(ro, rd, n, g, lat, sl.bytes, counts, nruns, runs,
+                                             walk_counter, status, s)
+                  : launch_walk<false, false>(ro, rd, n, g, lat, 0, counts, nruns, runs,
+                                              walk_counter, status, s);
+    if (st != HDDA_OK) return st;
+  }
+  {
+    KernelTimer kt(vdb ? "hdda_emit" : "dense_emit", s);
+    if (vdb)
+      emit_kernel<true><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, counts, nruns, runs,
+                                                     offsets, ray_idx, t0, t1, capacity, state,
+                                                     emit_counter, status, total);
+    else
+      emit_kernel<false><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, counts, nruns, runs,
+                                                      offsets, ray_idx, t0, t1, capacity, state,
+                                                      emit_counter, status, total);
+  }
+  HDDA_CUDA_TRY(cudaGetLastError());
+  return finish(hw, scratch, capacity, total_out, s);
+}
+
+int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+             const hdda_params* params, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
+             int64_t capacity, int64_t* total_out, cudaStream_t s) {
+  clear_error();
+  int st = check_args(vdb, ro, rd, n, grid, params, offsets, ray_idx, t0, t1, capacity,
+                      total_out);
+  if (st != HDDA_OK) return st;
   LatticeDev lat;
   st = get_lattice(*params, s, &lat);
   if (st != HDDA_OK) return st;
@@ -515,63 +1031,13 @@ int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_g
     HDDA_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
     return HDDA_OK;
   }
-  const GridDev g = grid->view();
-  const unsigned nb = (unsigned)((n + kBS - 1) / kBS);
-  // scratch: [ticket u32, status u32, total i64] + tile_sum[nb] + tile_prefix[nb]
-  char* scratch = nullptr;
-  HDDA_CUDA_TRY(cudaMallocAsync(&scratch, 16 + 16 * (size_t)nb, s));
-  unsigned* ticket = reinterpret_cast<unsigned*>(scratch);
-  unsigned* status = ticket + 1;
-  int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
-  int64_t* tile_sum = reinterpret_cast<int64_t*>(scratch + 16);
-  int64_t* tile_prefix = tile_sum + nb;
   int64_t* hw = nullptr;
   st = host_words(&hw);
-  if (st == HDDA_OK) {
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);
-    if (e == cudaSuccess) {
-      KernelTimer kt(vdb ? "hdda_count" : "dense_count", s);
-      if (vdb)
-        count_kernel<true><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_sum, tile_prefix,
-                                              ticket, status, total);
-      else
-        count_kernel<false><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_sum,
-                                               tile_prefix, ticket, status, total);
-      kt.stop();
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hw, scratch, 16, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = cuda_error(e, "count pass");
-  }
-  if (st == HDDA_OK) {
-    const unsigned dev_status = reinterpret_cast<unsigned*>(hw)[1];
-    const int64_t tot = hw[1];
-    *total_out = tot;
-    if (dev_status & kDevInternal) {
-      st = set_error(HDDA_ERR_INTERNAL, "region check failed on the device");
-    } else if (capacity == 0) {
-      KernelTimer kt("offsets", s);
-      offsets_kernel<<<nb, kBS, 0, s>>>(n, offsets, tile_prefix, total);
-      kt.stop();
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) st = cuda_error(e, "offsets_kernel");
-    } else if (capacity < tot) {
-      st = set_error(HDDA_ERR_CAPACITY, "capacity %lld < %lld samples", (long long)capacity,
-                     (long long)tot);
-    } else {
-      KernelTimer kt(vdb ? "hdda_emit" : "dense_emit", s);
-      if (vdb)
-        emit_kernel<true><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_prefix, total,
-                                             ray_idx, t0, t1, status);
-      else
-        emit_kernel<false><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_prefix, total,
-                                              ray_idx, t0, t1, status);
-      kt.stop();
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) st = cuda_error(e, "emit_kernel");
-    }
-  }
+  if (st != HDDA_OK) return st;
+  char* scratch = nullptr;
+  HDDA_CUDA_TRY(cudaMallocAsync(&scratch, twopass_scratch_bytes(n), s));
+  st = run_twopass(vdb, ro, rd, n, grid, lat, offsets, ray_idx, t0, t1, capacity, total_out,
+                   scratch, hw, s);
   cudaError_t e = cudaFreeAsync(scratch, s);
   if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
   return st;
@@ -582,17 +1048,11 @@ int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_g
 // ---------------------------------------------------------------------------
 // traversal over caller-provided scratch (no allocation of any kind)
 // ---------------------------------------------------------------------------
-// Scratch layout: [0,256) header {ticket u32, status u32, total i64,
-// lattice count i64, lattice limit flag i64}; then t[max_k + 1] and
-// tm[max_k] floats; then tile_sum[max_tiles] and tile_prefix[max_tiles].
-
-namespace {
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-}  // namespace
+// Scratch layout: [0, 256) lattice read-back words; then one lattice block
+// of capacity max_k; then the sampler's 32-byte header and tile states.
 
 size_t traverse_scratch_bytes(int max_k, int64_t max_tiles) {
-  return 256 + align256(sizeof(float) * (2 * (size_t)max_k + 1)) +
-         2 * sizeof(int64_t) * (size_t)max_tiles;
+  return 256 + lattice_block_bytes(max_k) + 32 + 8 * (size_t)max_tiles;
 }
 
 int64_t traverse_rays_per_tile() { return kBS; }
@@ -603,49 +1063,24 @@ int traverse_with_scratch(bool vdb, const float* ro, const float* rd, int64_t n,
                           int64_t* total_out, void* scratch, int max_k, int64_t max_tiles,
                           cudaStream_t s) {
   clear_error();
-  if (!grid) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
-  if (grid->kind != (vdb ? HDDA_GRID_VDB : HDDA_GRID_DENSE))
-    return set_error(HDDA_ERR_INVALID_ARG, vdb ? "hdda traversal needs a VDB grid"
-                                               : "dense traversal needs a dense grid");
-  if (n < 0 || n > INT32_MAX) return set_error(HDDA_ERR_INVALID_ARG, "n_rays=%lld", (long long)n);
+  int st = check_args(vdb, ro, rd, n, grid, params, offsets, ray_idx, t0, t1, capacity,
+                      total_out);
+  if (st != HDDA_OK) return st;
   const int64_t nb = (n + kBS - 1) / kBS;
   if (nb > max_tiles)
     return set_error(HDDA_ERR_INVALID_ARG,
                      "n_rays=%lld exceeds the static scratch maximum of %lld rays",
                      (long long)n, (long long)(max_tiles * kBS));
-  if (!offsets || !total_out) return set_error(HDDA_ERR_INVALID_ARG, "offsets/total_out NULL");
-  if (n > 0 && (!ro || !rd)) return set_error(HDDA_ERR_INVALID_ARG, "rays NULL");
-  if (capacity < 0) return set_error(HDDA_ERR_INVALID_ARG, "capacity < 0");
-  if (capacity > 0 && (!ray_idx || !t0 || !t1))
-    return set_error(HDDA_ERR_INVALID_ARG, "sample outputs NULL with capacity > 0");
   if (!scratch) return set_error(HDDA_ERR_INVALID_ARG, "scratch is NULL");
-  int st = validate_params(params);
-  if (st != HDDA_OK) return st;
-  int dev = 0;
-  HDDA_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev != grid->device)
-    return set_error(HDDA_ERR_INVALID_ARG, "grid lives on device %d, current is %d",
-                     grid->device, dev);
   *total_out = 0;
-
   char* base = static_cast<char*>(scratch);
-  unsigned* ticket = reinterpret_cast<unsigned*>(base);
-  unsigned* status = ticket + 1;
-  int64_t* total = reinterpret_cast<int64_t*>(base + 8);
-  int64_t* lat_words = reinterpret_cast<int64_t*>(base + 16);
-  float* lat_t = reinterpret_cast<float*>(base + 256);
-  float* lat_tm = lat_t + max_k + 1;
-  int64_t* tile_sum =
-      reinterpret_cast<int64_t*>(base + 256 + align256(sizeof(float) * (2 * (size_t)max_k + 1)));
-  int64_t* tile_prefix = tile_sum + max_tiles;
+  int64_t* lat_words = reinterpret_cast<int64_t*>(base);
+  char* block = base + 256;
+  char* sampler_scratch = block + lattice_block_bytes(max_k);
 
-  // The array keeps the previous call's contents: clear the counters first.
+  // The array keeps the previous call's contents: clear what is read first.
   HDDA_CUDA_TRY(cudaMemsetAsync(base, 0, 32, s));
-  hdda_params key;
-  std::memset(&key, 0, sizeof(key));
-  key.near_t = params->near_t; key.far_t = params->far_t; key.step = params->step;
-  key.cone_angle = params->cone_angle; key.max_step = params->max_step;
-  key.max_steps = params->max_steps;
+  const hdda_params key = canonical(*params);
   lattice_count_kernel<<<1, 1, 0, s>>>(key, lat_words);
   HDDA_CUDA_TRY(cudaGetLastError());
   int64_t hw[2] = {0, 0};  // pageable host words: no host allocation either
@@ -658,44 +1093,15 @@ int traverse_with_scratch(bool vdb, const float* ro, const float* rd, int64_t n,
     return set_error(HDDA_ERR_INVALID_ARG,
                      "lattice of %lld candidates exceeds the static scratch maximum of %d",
                      (long long)hw[0], max_k);
-  const LatticeDev lat{lat_t, lat_tm, (int)hw[0]};
-  lattice_fill_kernel<<<1, 1, 0, s>>>(key, lat.K, lat_t, lat_tm);
+  const int K = (int)hw[0];
+  lattice_fill_kernel<<<1, 1, 0, s>>>(key, K, max_k, block);
   HDDA_CUDA_TRY(cudaGetLastError());
   if (n == 0) {
     HDDA_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
     return HDDA_OK;
   }
-  const GridDev g = grid->view();
-  if (vdb)
-    count_kernel<true><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_sum,
-                                                    tile_prefix, ticket, status, total);
-  else
-    count_kernel<false><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_sum,
-                                                     tile_prefix, ticket, status, total);
-  HDDA_CUDA_TRY(cudaGetLastError());
-  HDDA_CUDA_TRY(cudaMemcpyAsync(hw, base, 16, cudaMemcpyDeviceToHost, s));
-  HDDA_CUDA_TRY(cudaStreamSynchronize(s));
-  const unsigned dev_status = reinterpret_cast<unsigned*>(hw)[1];
-  const int64_t tot = hw[1];
-  *total_out = tot;
-  if (dev_status & kDevInternal)
-    return set_error(HDDA_ERR_INTERNAL, "region check failed on the device");
-  if (capacity == 0) {
-    offsets_kernel<<<(unsigned)nb, kBS, 0, s>>>(n, offsets, tile_prefix, total);
-    HDDA_CUDA_TRY(cudaGetLastError());
-    return HDDA_OK;
-  }
-  if (capacity < tot)
-    return set_error(HDDA_ERR_CAPACITY, "capacity %lld < %lld samples", (long long)capacity,
-                     (long long)tot);
-  if (vdb)
-    emit_kernel<true><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_prefix,
-                                                   total, ray_idx, t0, t1, status);
-  else
-    emit_kernel<false><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, tile_prefix,
-                                                    total, ray_idx, t0, t1, status);
-  HDDA_CUDA_TRY(cudaGetLastError());
-  return HDDA_OK;
+  return run_onepass(vdb, ro, rd, n, grid, lattice_view(block, max_k, K), offsets, ray_idx, t0,
+                     t1, capacity, total_out, sampler_scratch, hw, s);
 }
 
 }  // namespace hdda

@@ -271,14 +271,20 @@ def test_edge_cases(H):
     full = H.traverse_dense(ot, dt, gd, prm)
     assert c.total == full.total
     np.testing.assert_array_equal(to_np(c.offsets), to_np(full.offsets))
-    # capacity below the total is an error that writes no samples
-    small = H.alloc_samples(o.shape[0], max(1, full.total - 1))
-    small.t0.fill_(-1.0)
+    # capacity below the total is an error that writes nothing at or past capacity
+    cap = max(1, full.total - 100)
+    big = H.alloc_samples(o.shape[0], full.total)
+    for t in (big.t0, big.t1):
+        t.fill_(-1.0)
+    big.ray_idx.fill_(-7)
+    small = H.Samples(big.offsets, big.ray_idx[:cap], big.t0[:cap], big.t1[:cap], 0)
     with pytest.raises(H.HddaError) as ex:
         H.traverse_hdda(ot, dt, gv, prm, out=small)
     assert ex.value.code == H.ERR_CAPACITY
     assert small.total == full.total
-    assert bool((small.t0 == -1.0).all())
+    assert bool((big.t0[cap:] == -1.0).all()) and bool((big.ray_idx[cap:] == -7).all())
+    # what was written below capacity is the true prefix of the sample set
+    np.testing.assert_array_equal(to_np(big.t0[:cap]), to_np(full.t0[:cap]))
     # more candidates than max_steps
     with pytest.raises(H.HddaError) as ex:
         H.traverse_hdda(ot, dt, gv, H.make_params(2.0, 6.0, 5e-3, max_steps=100))
