@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 # + 2 fma (squared distance), 1 mul (exponent scale), 1 mul (amplitude),
 # 1 add (density), 3 fma (colour); the exp2 runs on the MUFU pipe alongside.
 COMPOSITE_FP32_PER_BLOB = 12
-KERNELS_PER_TIMER = {"build_vdb": 4}
+KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 
 
 def parse_args():
@@ -141,7 +141,10 @@ def run_ours(args):
     prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
     gv = hdda.build_vdb(dense, sc.aabbs)
     gd = hdda.pack_dense(dense, sc.aabbs)
+    gvp = hdda.build_vdb(dense, sc.aabbs)   # the plain VDB tree, without refinement masks
+    gvp.set_refine(False)
     vstats = gv.stats()
+    plain_bytes = int(gvp.stats().bytes)
 
     totals = [hdda.traverse_hdda(O[c], D[c], gv, prm, count_only=True).total
               for c in range(N_CAMERAS)]
@@ -171,6 +174,10 @@ def run_ours(args):
     def sampler_hdda(j):
         c = cam_of(j)
         return hdda.traverse_hdda(O[c], D[c], gv, prm, out=bufs).total
+
+    def sampler_hdda_plain(j):
+        c = cam_of(j)
+        return hdda.traverse_hdda(O[c], D[c], gvp, prm, out=bufs).total
 
     def sampler_dense(j):
         c = cam_of(j)
@@ -220,6 +227,7 @@ def run_ours(args):
     ms_dense, samples_dense, kern_dense, _ = timed(step_dense, max(3, K // 2), 2, profile=True)
     ms_sh, samp_sh, _, _ = timed(sampler_hdda, K, 2)
     ms_sd, samp_sd, _, _ = timed(sampler_dense, max(3, K // 2), 2)
+    ms_sp, samp_sp, _, _ = timed(sampler_hdda_plain, max(3, K // 2), 2)
 
     total_rays = n * K * world
     value = total_rays / (ms / 1e3)
@@ -308,11 +316,12 @@ def run_ours(args):
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
     roofline = roof(dom) if dom else None
     # the sampler as a whole (walk + emit): rays in, CSR offsets and samples out
-    sam_ms = sum(kern[k][1] / max(1, kern[k][0]) for k in ("hdda_walk", "hdda_emit") if k in kern)
+    sam_k = ("hdda_walk", "tile_scan", "hdda_emit")
+    sam_ms = sum(kern[k][1] / max(1, kern[k][0]) for k in sam_k if k in kern)
     roofline_sampler = None
     if sam_ms > 0:
         ach = sampler_bytes / (sam_ms / 1e3) / 1e9
-        roofline_sampler = {"kernels": ["hdda_walk", "hdda_emit"], "bound": "hbm",
+        roofline_sampler = {"kernels": list(sam_k), "bound": "hbm",
                             "alg_bytes": int(sampler_bytes), "ms": round(sam_ms, 4),
                             "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                             "frac": round(ach / hbm_peak, 4), "peak_source": peak_src}
@@ -346,10 +355,15 @@ def run_ours(args):
         "dense_dda_sampler": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_sd / 1e3), 1),
                               "samples_per_s": round(samp_sd * world / (ms_sd / 1e3), 1),
                               "ms_per_frame": round(ms_sd / max(3, K // 2), 4)},
+        "hdda_plain_vdb_sampler": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_sp / 1e3), 1),
+                                   "ms_per_frame": round(ms_sp / max(3, K // 2), 4),
+                                   "note": "HDDA on the plain VDB tree (8^3 leaves, 16^3-block "
+                                           "nodes), refinement masks off"},
         "dense_dda_step": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_dense / 1e3), 1),
                            "ms_per_step": round(ms_dense / max(3, K // 2), 4)},
         "hdda_vs_dense_sampler_speedup": round(ms_sd / max(3, K // 2) / (ms_sh / K), 3),
-        "grid": {"vdb_bytes": grid_bytes, "dense_bytes": int(vstats.dense_bytes),
+        "grid": {"vdb_bytes": grid_bytes, "vdb_plain_bytes": plain_bytes,
+                 "dense_bytes": int(vstats.dense_bytes),
                  "n_leaves": int(vstats.n_leaves), "n_tiles": int(vstats.n_tiles)},
         "kernels": per_kernel,
         "kernels_dense_step": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}

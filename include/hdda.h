@@ -131,7 +131,19 @@ typedef enum {
     HDDA_ARRAY_LEAF_PREFIX = 4,
     /* uint32 [n_leaves][16]: 512-bit leaf masks in (level, node, cell)
        order; voxel (x%8, y%8, z%8) is bit ((x%8)*8 + y%8)*8 + z%8 (VDB).    */
-    HDDA_ARRAY_LEAVES = 5
+    HDDA_ARRAY_LEAVES = 5,
+    /* uint32 [levels][nodes^3][18] refinement masks of each node (VDB): words
+       0-1 = 64 bits, one per 32^3-voxel group g = (gx*4 + gy)*4 + gz with
+       gc = (voxel_c % 128) / 32; words 2-17 = 512 bits, one per 16^3-voxel
+       group g = (gx*8 + gy)*8 + gz with gc = (voxel_c % 128) / 16.  A bit is
+       set when the group holds an occupied voxel.                           */
+    HDDA_ARRAY_NODE_SUPER = 6,
+    /* uint32 [n_leaves][3] refinement masks of each leaf (VDB), leaf order as
+       HDDA_ARRAY_LEAVES: words 0-1 = 64 bits, one per 2^3-voxel cell
+       c = (cx*4 + cy)*4 + cz with cc = (voxel_c % 8) / 2; word 2 = 8 bits,
+       one per 4^3-voxel cell c = (cx*2 + cy)*2 + cz with cc = (voxel_c % 8)
+       / 4.  A bit is set when the cell holds an occupied voxel.             */
+    HDDA_ARRAY_LEAF_SUB = 7
 } hdda_array;
 
 /* Version string of the library. */
@@ -183,6 +195,17 @@ int hdda_grid_stats_get(const hdda_grid* grid, hdda_grid_stats* out);
  */
 int hdda_grid_copy_array(const hdda_grid* grid, int which, void* dst, size_t bytes,
                          size_t* needed);
+
+/*
+ * Chooses the hierarchy hdda_traverse_hdda walks on a VDB grid.  on = 1 (the
+ * default): besides empty nodes, empty or tiled 8^3 blocks and single leaf
+ * voxels, it also crosses empty 32^3 and 16^3 groups inside a node and
+ * empty 4^3 and 2^3 cells inside a leaf in one step each, an octree-style
+ * refinement of the VDB tree (Sec. 5 names finer subdivision as worth
+ * studying).  on = 0: the plain tree of 8^3 leaves under 16^3-block nodes.
+ * Results are identical either way.  Not for dense grids.
+ */
+int hdda_grid_set_refine(hdda_grid* grid, int on);
 
 /* Frees a grid (waits for the device to finish with it).  NULL is a no-op. */
 void hdda_grid_free(hdda_grid* grid);

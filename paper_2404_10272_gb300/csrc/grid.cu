@@ -15,6 +15,11 @@
 //                       leaf prefix per mask word, leaf and tile totals
 //   vdb_scatter_kernel  16 threads per partial block copy its mask into the
 //                       compact leaf pool
+// The node and scatter kernels also write the refinement masks (occupied
+// 32^3 and 16^3 groups per node, occupied 4^3 and 2^3 cells per leaf) that
+// let hierarchical DDA cross empty space in power-of-two steps below and
+// above the 8^3 leaf, in the manner of an octree (Sec. 5 suggests finer
+// subdivision).
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -136,8 +141,11 @@ __global__ void vdb_nodes_kernel(int L, int B, int N, const uint8_t* __restrict_
                                  uint32_t* __restrict__ local_prefix,
                                  uint32_t* __restrict__ node_leaves,
                                  uint32_t* __restrict__ node_tiles,
-                                 uint32_t* __restrict__ nstate) {
+                                 uint32_t* __restrict__ nstate,
+                                 uint32_t* __restrict__ nsuper) {
   __shared__ uint32_t warp_tot[33];
+  __shared__ uint32_t s_occ[kNodeWords];  // child | tile
+  __shared__ uint32_t s_g16[16];          // occupied 16^3 groups
   const int64_t N3 = (int64_t)N * N * N;
   const int64_t B3 = (int64_t)B * B * B;
   const int64_t ng = blockIdx.x;
@@ -173,6 +181,35 @@ __global__ void vdb_nodes_kernel(int L, int B, int N, const uint8_t* __restrict_
     else if (leaves == 0 && tiles == incells) st = kNodeFull;
     nstate[ng] = st;
   }
+  // refinement: 16^3-voxel groups are 2^3 cells, 32^3-voxel groups 2^3 of those
+  s_occ[w] = my_child | my_tile;
+  __syncthreads();
+  for (int j = 0; j < 4; ++j) {
+    const int g2 = j * kNodeWords + threadIdx.x;  // 0..511
+    const int gx = g2 >> 6, gy = (g2 >> 3) & 7, gz = g2 & 7;
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int cell = ((2 * gx + (a >> 2)) * 16 + (2 * gy + ((a >> 1) & 1))) * 16 + 2 * gz + (a & 1);
+      any |= (s_occ[cell >> 5] >> (cell & 31)) & 1u;
+    }
+    const uint32_t bal = __ballot_sync(kFull, any);
+    if (lane == 0) s_g16[g2 >> 5] = bal;
+  }
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int g4 = threadIdx.x;
+    const int gx = g4 >> 4, gy = (g4 >> 2) & 3, gz = g4 & 3;
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int g2 = ((2 * gx + (a >> 2)) * 8 + (2 * gy + ((a >> 1) & 1))) * 8 + 2 * gz + (a & 1);
+      any |= (s_g16[g2 >> 5] >> (g2 & 31)) & 1u;
+    }
+    const uint32_t bal = __ballot_sync(kFull, any);
+    if (lane == 0) nsuper[ng * kSuperWords + warp] = bal;
+  }
+  if (threadIdx.x < 16) nsuper[ng * kSuperWords + 2 + threadIdx.x] = s_g16[threadIdx.x];
 }
 
 constexpr int kMaxNodesTotal = HDDA_MAX_LEVELS * (HDDA_MAX_RES / kNodeVox) *
@@ -209,7 +246,7 @@ __global__ void vdb_scatter_kernel(int L, int B, int N, const uint8_t* __restric
                                    const uint32_t* __restrict__ blk_masks,
                                    const uint32_t* __restrict__ child,
                                    const uint32_t* __restrict__ prefix,
-                                   uint32_t* __restrict__ leaves) {
+                                   uint32_t* __restrict__ leaves, uint32_t* __restrict__ lsub) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t blk = t >> 4;
   const int part = (int)(t & 15);
@@ -226,6 +263,26 @@ __global__ void vdb_scatter_kernel(int L, int B, int N, const uint8_t* __restric
   const uint32_t bit = 1u << (cell & 31);
   const uint32_t leaf = prefix[ng * kNodeWords + w] + __popc(child[ng * kNodeWords + w] & (bit - 1u));
   leaves[(int64_t)leaf * kLeafWords + part] = blk_masks[blk * kLeafWords + part];
+  if (part == 0) {
+    const uint32_t* m = blk_masks + blk * kLeafWords;
+    uint32_t c2lo = 0, c2hi = 0, c4 = 0;
+    for (int cell = 0; cell < 64; ++cell) {  // 2^3 cells, (cx*4 + cy)*4 + cz
+      const int cx = cell >> 4, cy = (cell >> 2) & 3, cz = cell & 3;
+      bool any = false;
+      for (int a = 0; a < 8; ++a) {
+        const int v = ((2 * cx + (a >> 2)) * 8 + (2 * cy + ((a >> 1) & 1))) * 8 + 2 * cz + (a & 1);
+        any |= (m[v >> 5] >> (v & 31)) & 1u;
+      }
+      if (any) {
+        if (cell < 32) c2lo |= 1u << cell;
+        else c2hi |= 1u << (cell - 32);
+        c4 |= 1u << (((cx >> 1) * 2 + (cy >> 1)) * 2 + (cz >> 1));
+      }
+    }
+    lsub[(int64_t)leaf * kLeafSubWords + 0] = c2lo;
+    lsub[(int64_t)leaf * kLeafSubWords + 1] = c2hi;
+    lsub[(int64_t)leaf * kLeafSubWords + 2] = c4;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -276,6 +333,8 @@ size_t layout(hdda_grid* g, char* base) {
   carve(base, off, g->prefix, nw, vdb);
   carve(base, off, g->nstate, g->nodes_total(), vdb);
   carve(base, off, g->leaves, g->blocks_total() * kLeafWords, vdb);
+  carve(base, off, g->nsuper, g->nodes_total() * kSuperWords, vdb);
+  carve(base, off, g->lsub, g->blocks_total() * kLeafSubWords, vdb);
   carve(base, off, g->blk_masks, g->blocks_total() * kLeafWords, vdb);
   carve(base, off, g->blk_state, g->blocks_total(), vdb);
   carve(base, off, g->local_prefix, nw, vdb);
@@ -302,13 +361,13 @@ int launch_build(hdda_grid* g, const uint8_t* dense, cudaStream_t s) {
     HDDA_CUDA_TRY(cudaGetLastError());
     vdb_nodes_kernel<<<(unsigned)g->nodes_total(), kNodeWords, 0, s>>>(
         g->L, g->B, g->N, g->blk_state, g->child, g->tile, g->local_prefix, g->node_leaves,
-        g->node_tiles, g->nstate);
+        g->node_tiles, g->nstate, g->nsuper);
     HDDA_CUDA_TRY(cudaGetLastError());
     vdb_finalize_kernel<<<1, 1024, 0, s>>>(g->nodes_total(), g->node_leaves, g->node_tiles,
                                           g->local_prefix, g->prefix, g->totals);
     HDDA_CUDA_TRY(cudaGetLastError());
     vdb_scatter_kernel<<<blocks_for(nblk * 16, 256), 256, 0, s>>>(
-        g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves);
+        g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves, g->lsub);
     kt.stop();
     HDDA_CUDA_TRY(cudaGetLastError());
   }
@@ -359,6 +418,7 @@ int64_t structure_bytes(const hdda_grid* g, int64_t n_leaves) {
   } else {
     b += g->nodes_total() * (3 * kNodeWords * 4 + 4);
     b += n_leaves * kLeafWords * 4;
+    if (g->refine) b += g->nodes_total() * kSuperWords * 4 + n_leaves * kLeafSubWords * 4;
   }
   return b;
 }
@@ -427,13 +487,18 @@ extern "C" int hdda_grid_copy_array(const hdda_grid* g, int which, void* dst, si
     case HDDA_ARRAY_TILE_MASK: if (vdb) { src = g->tile; n = nw; } break;
     case HDDA_ARRAY_LEAF_PREFIX: if (vdb) { src = g->prefix; n = nw; } break;
     case HDDA_ARRAY_LEAVES:
+    case HDDA_ARRAY_LEAF_SUB:
       if (vdb) {
         hdda_grid_stats gs;
         int st = hdda_grid_stats_get(g, &gs);
         if (st != HDDA_OK) return st;
-        src = g->leaves;
-        n = (size_t)gs.n_leaves * kLeafWords * 4;
+        const bool sub = which == HDDA_ARRAY_LEAF_SUB;
+        src = sub ? g->lsub : g->leaves;
+        n = (size_t)gs.n_leaves * (sub ? kLeafSubWords : kLeafWords) * 4;
       }
+      break;
+    case HDDA_ARRAY_NODE_SUPER:
+      if (vdb) { src = g->nsuper; n = (size_t)g->nodes_total() * kSuperWords * 4; }
       break;
     default: break;
   }
@@ -443,6 +508,15 @@ extern "C" int hdda_grid_copy_array(const hdda_grid* g, int which, void* dst, si
   if (bytes < n) return set_error(HDDA_ERR_CAPACITY, "array needs %zu bytes, got %zu", n, bytes);
   HDDA_CUDA_TRY(cudaEventSynchronize(g->built));
   if (n) HDDA_CUDA_TRY(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
+  return HDDA_OK;
+}
+
+extern "C" int hdda_grid_set_refine(hdda_grid* g, int on) {
+  clear_error();
+  if (!g) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
+  if (g->kind != HDDA_GRID_VDB)
+    return set_error(HDDA_ERR_INVALID_ARG, "refinement applies to VDB grids");
+  g->refine = on ? 1 : 0;
   return HDDA_OK;
 }
 

@@ -21,6 +21,9 @@ struct hdda_grid {
   uint32_t* prefix = nullptr;    // vdb [L*N^3][128]
   uint32_t* nstate = nullptr;    // vdb [L*N^3]
   uint32_t* leaves = nullptr;    // vdb [L*B^3][16] capacity, compact prefix used
+  uint32_t* nsuper = nullptr;    // vdb [L*N^3][kSuperWords] refinement masks
+  uint32_t* lsub = nullptr;      // vdb [L*B^3][kLeafSubWords] capacity, per leaf
+  int refine = 1;                // HDDA uses the refinement masks
   // build temporaries (kept so that a rebuild allocates nothing)
   uint32_t* blk_masks = nullptr; // [L*B^3][16]
   uint8_t* blk_state = nullptr;  // [L*B^3]
@@ -48,6 +51,7 @@ struct hdda_grid {
     }
     g.thr = thr; g.bits = bits; g.child = child; g.tile = tile;
     g.prefix = prefix; g.nstate = nstate; g.leaves = leaves;
+    g.nsuper = nsuper; g.lsub = lsub;
     return g;
   }
 };

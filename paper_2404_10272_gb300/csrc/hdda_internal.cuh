@@ -21,6 +21,15 @@ constexpr int kNodeDim = 16;     // node edge in blocks (16^3 blocks)
 constexpr int kNodeVox = kBlockDim * kNodeDim;  // 128 voxels per node edge
 constexpr int kNodeWords = 4096 / 32;           // 128 mask words per node
 constexpr int kLeafWords = 512 / 32;            // 16 words per leaf
+// Refinement masks (set bit = the group holds some occupied voxel):
+//   per node: 64 bits for its 4^3 groups of 32^3 voxels, then 512 bits for
+//   its 8^3 groups of 16^3 voxels;  per leaf: 64 bits for its 4^3 cells of
+//   2^3 voxels, then 8 bits for its 2^3 cells of 4^3 voxels.
+constexpr int kSuperWords = 2 + 16;
+constexpr int kLeafSubWords = 3;
+
+// Walk variants: dense bit array, VDB tree, VDB tree with refinement masks.
+enum WalkMode : int { kModeDense = 0, kModeVdb = 1, kModeVdbRefined = 2 };
 
 enum NodeState : uint32_t { kNodeEmpty = 0, kNodeMixed = 1, kNodeFull = 2 };
 enum BlockState : uint8_t { kBlockEmpty = 0, kBlockPartial = 1, kBlockFull = 2 };
@@ -54,6 +63,8 @@ struct GridDev {
   const uint32_t* prefix;    // vdb: [L*N^3][128] global leaf index per word
   const uint32_t* nstate;    // vdb: [L*N^3]
   const uint32_t* leaves;    // vdb: [n_leaves][16]
+  const uint32_t* nsuper;    // vdb: [L*N^3][kSuperWords]
+  const uint32_t* lsub;      // vdb: [n_leaves][kLeafSubWords]
 };
 
 // Buckets of the lattice's inverse index (t -> k), over binary32 keys.

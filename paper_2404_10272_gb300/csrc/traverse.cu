@@ -179,10 +179,11 @@ struct Tabs {
   const uint32_t* tile;
   const uint32_t* prefix;
   const uint32_t* nstate;
+  const uint32_t* nsuper;
 };
 
 __device__ __forceinline__ Tabs global_tabs(const GridDev& g) {
-  return Tabs{g.thr, g.child, g.tile, g.prefix, g.nstate};
+  return Tabs{g.thr, g.child, g.tile, g.prefix, g.nstate, g.nsuper};
 }
 
 // x = o + tm * d per axis, one rounding per operation.
@@ -214,8 +215,8 @@ __device__ __forceinline__ void clip_cells(float e[3], const Ray& r, const float
 }
 
 // Classifies x and sets e to the region holding it.  Returns its occupancy.
-// kSm: thresholds and node arrays of g point into shared memory.
-template <bool kVdb, bool kSm>
+// kSm: the tables in tb point into shared memory.
+template <int kMode, bool kSm>
 __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const Ray& r,
                                        const float x[3], float e[3]) {
 #pragma unroll
@@ -267,7 +268,7 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
   }
   const int R1 = g.R + 1;
   const float* thr = tb.thr + (int64_t)l * 3 * R1;
-  if (!kVdb) {
+  if constexpr (kMode == kModeDense) {
     const int64_t lin = ((int64_t)i[0] * g.R + i[1]) * g.R + i[2];
     const uint32_t w = __ldg(g.bits + (int64_t)l * g.W + (lin >> 5));
 #pragma unroll
@@ -287,6 +288,28 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
     }
     return st == kNodeFull;
   }
+  if constexpr (kMode == kModeVdbRefined) {
+    // empty 32^3 group, then empty 16^3 group of the node
+    const uint32_t* ns = tb.nsuper + ng * kSuperWords;
+    const int g4 = (((i[0] >> 5) & 3) * 4 + ((i[1] >> 5) & 3)) * 4 + ((i[2] >> 5) & 3);
+    if (!((ld<kSm>(ns + (g4 >> 5)) >> (g4 & 31)) & 1u)) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int a0 = i[c] & ~31;
+        clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 32, g.R));
+      }
+      return false;
+    }
+    const int g2 = (((i[0] >> 4) & 7) * 8 + ((i[1] >> 4) & 7)) * 8 + ((i[2] >> 4) & 7);
+    if (!((ld<kSm>(ns + 2 + (g2 >> 5)) >> (g2 & 31)) & 1u)) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int a0 = i[c] & ~15;
+        clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 16, g.R));
+      }
+      return false;
+    }
+  }
   // block level: empty or tile
   const int cell = (((i[0] >> 3) & 15) * 16 + ((i[1] >> 3) & 15)) * 16 + ((i[2] >> 3) & 15);
   const int w = cell >> 5;
@@ -303,6 +326,28 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
   }
   // voxel of a leaf
   const uint32_t leaf = ld<kSm>(tb.prefix + ng * kNodeWords + w) + __popc(cw & (bit - 1u));
+  if constexpr (kMode == kModeVdbRefined) {
+    // empty 4^3 cell, then empty 2^3 cell of the leaf
+    const uint32_t* ls = g.lsub + (int64_t)leaf * kLeafSubWords;
+    const int c4 = (((i[0] >> 2) & 1) * 2 + ((i[1] >> 2) & 1)) * 2 + ((i[2] >> 2) & 1);
+    if (!((__ldg(ls + 2) >> c4) & 1u)) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int a0 = i[c] & ~3;
+        clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 4, g.R));
+      }
+      return false;
+    }
+    const int c2 = (((i[0] >> 1) & 3) * 4 + ((i[1] >> 1) & 3)) * 4 + ((i[2] >> 1) & 3);
+    if (!((__ldg(ls + (c2 >> 5)) >> (c2 & 31)) & 1u)) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int a0 = i[c] & ~1;
+        clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 2, g.R));
+      }
+      return false;
+    }
+  }
   const int v = ((i[0] & 7) * 8 + (i[1] & 7)) * 8 + (i[2] & 7);
   const uint32_t lw = __ldg(g.leaves + (int64_t)leaf * kLeafWords + (v >> 5));
 #pragma unroll
@@ -375,7 +420,7 @@ __device__ __forceinline__ int cross(const Ray& r, const LatticeDev& lat, const 
 // [k_begin, k_end): the first kMaxRuns go to runs[j * stride]; nruns counts
 // all.  With kEmit it instead writes the samples from `out`, below
 // `capacity` (lat.t must then be a global-memory table).
-template <bool kVdb, bool kEmit, bool kSm>
+template <int kMode, bool kEmit, bool kSm>
 __device__ __forceinline__ int64_t walk(const GridDev& g, const Tabs& tb, const LatticeDev& lat,
                                         const LatHdr& h, const Ray& r, uint2* runs,
                                         int64_t stride, int& nruns, int32_t rid,
@@ -392,7 +437,7 @@ __device__ __forceinline__ int64_t walk(const GridDev& g, const Tabs& tb, const 
   int k = 0;
   while (k < K) {
     float e[3];
-    const bool occ = locate<kVdb, kSm>(g, tb, r, x, e);
+    const bool occ = locate<kMode, kSm>(g, tb, r, x, e);
     if (outside(x, e, r)) atomicOr(status, kDevInternal);  // region must hold its point
     const int kn = cross<kSm>(r, lat, h, k, e, x);
     if (occ) {
@@ -573,7 +618,7 @@ __device__ __forceinline__ void expand_warp(int64_t off, int64_t c, bool overflo
 // one-pass sampler (bounded scratch: runs stay in shared memory)
 // ---------------------------------------------------------------------------
 
-template <bool kVdb>
+template <int kMode>
 __global__ void __launch_bounds__(kBS) onepass_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx,
@@ -596,7 +641,7 @@ __global__ void __launch_bounds__(kBS) onepass_kernel(
   if (r < n) {
     valid = load_ray(ro, rd, r, ray);
     if (valid)
-      c = walk<kVdb, false, false>(g, global_tabs(g), lat, h, ray, s_runs + threadIdx.x, kBS,
+      c = walk<kMode, false, false>(g, global_tabs(g), lat, h, ray, s_runs + threadIdx.x, kBS,
                                    nruns, 0, 0, 0, nullptr, nullptr, nullptr, status);
   }
   int64_t agg = 0;
@@ -619,7 +664,7 @@ __global__ void __launch_bounds__(kBS) onepass_kernel(
                     (int32_t)((int64_t)tile * kBS + warp * 32), lat.t, capacity, ray_idx, t0, t1);
   if (overflow && valid) {
     int unused = 0;
-    walk<kVdb, true, false>(g, global_tabs(g), lat, h, ray, nullptr, 0, unused, (int32_t)r, off,
+    walk<kMode, true, false>(g, global_tabs(g), lat, h, ray, nullptr, 0, unused, (int32_t)r, off,
                             capacity, ray_idx, t0, t1, status);
   }
 }
@@ -632,21 +677,24 @@ constexpr int kWalkBS = 256;
 
 // Shared-memory bytes that stage the walk's tables (0 = they do not fit).
 struct StageLayout {
-  size_t tm, kidx, thr, child, tile, prefix, nstate, bytes;
+  size_t tm, kidx, thr, child, tile, prefix, nstate, nsuper, bytes;
 };
 
-__host__ __device__ inline StageLayout stage_layout(int K, int L, int R, int64_t nodes, bool vdb) {
+__host__ __device__ inline StageLayout stage_layout(int K, int L, int R, int64_t nodes, int mode) {
   StageLayout s{};
   size_t o = 0;
   s.tm = o; o += sizeof(float) * (size_t)K;
   s.kidx = o; o += sizeof(int) * (size_t)(kKidxMax + 2);
   s.thr = o; o += sizeof(float) * (size_t)L * 3 * (R + 1);
-  s.child = s.tile = s.prefix = s.nstate = o;
-  if (vdb) {
+  s.child = s.tile = s.prefix = s.nstate = s.nsuper = o;
+  if (mode != kModeDense) {
     s.child = o; o += 4 * (size_t)nodes * kNodeWords;
     s.tile = o; o += 4 * (size_t)nodes * kNodeWords;
     s.prefix = o; o += 4 * (size_t)nodes * kNodeWords;
     s.nstate = o; o += 4 * (size_t)nodes;
+  }
+  if (mode == kModeVdbRefined) {
+    s.nsuper = o; o += 4 * (size_t)nodes * kSuperWords;
   }
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
@@ -662,11 +710,11 @@ __device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, in
 // Pass 1.  Persistent: each warp takes 32-ray tiles in order until none is
 // left, so a warp never waits for another.  Writes counts[r], nruns[r]
 // (saturated at 255) and the first kMaxRuns runs at runs[r + j * n].
-template <bool kVdb, bool kSm>
+template <int kMode, bool kSm>
 __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, int32_t* __restrict__ counts, uint8_t* __restrict__ nruns_out,
-    uint2* __restrict__ runs, unsigned* __restrict__ tile_counter,
+    uint2* __restrict__ runs, int64_t* __restrict__ tile_sum, unsigned* __restrict__ tile_counter,
     unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
@@ -674,7 +722,7 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
   LatticeDev ls = lat;
   if constexpr (kSm) {
     const int64_t nodes = (int64_t)g.L * g.N * g.N * g.N;
-    const StageLayout sl = stage_layout(lat.K, g.L, g.R, nodes, kVdb);
+    const StageLayout sl = stage_layout(lat.K, g.L, g.R, nodes, kMode);
     float* s_tm = reinterpret_cast<float*>(smem + sl.tm);
     int* s_kidx = reinterpret_cast<int*>(smem + sl.kidx);
     float* s_thr = reinterpret_cast<float*>(smem + sl.thr);
@@ -684,7 +732,7 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     ls.tm = s_tm;
     ls.kidx = s_kidx;
     tb.thr = s_thr;
-    if constexpr (kVdb) {
+    if constexpr (kMode != kModeDense) {
       uint32_t* s_child = reinterpret_cast<uint32_t*>(smem + sl.child);
       uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + sl.tile);
       uint32_t* s_prefix = reinterpret_cast<uint32_t*>(smem + sl.prefix);
@@ -698,6 +746,11 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
       tb.prefix = s_prefix;
       tb.nstate = s_nstate;
     }
+    if constexpr (kMode == kModeVdbRefined) {
+      uint32_t* s_nsuper = reinterpret_cast<uint32_t*>(smem + sl.nsuper);
+      stage_copy(s_nsuper, g.nsuper, nodes * kSuperWords);
+      tb.nsuper = s_nsuper;
+    }
     __syncthreads();
   }
   const int lane = threadIdx.x & 31;
@@ -708,70 +761,130 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     tile = __shfl_sync(kFull, tile, 0);
     if (tile >= ntiles) break;
     const int64_t r = (int64_t)tile * 32 + lane;
+    int64_t c = 0;
     if (r < n) {
       Ray ray;
       int nr = 0;
-      int64_t c = 0;
       if (load_ray(ro, rd, r, ray))
-        c = walk<kVdb, false, kSm>(g, tb, ls, h, ray, runs + r, n, nr, 0, 0, 0, nullptr, nullptr,
+        c = walk<kMode, false, kSm>(g, tb, ls, h, ray, runs + r, n, nr, 0, 0, 0, nullptr, nullptr,
                                    nullptr, status);
       counts[r] = (int32_t)c;
       nruns_out[r] = (uint8_t)min(nr, 255);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if (lane == 0) tile_sum[tile] = c;
   }
 }
 
-// Pass 2.  Each CTA loads 128 counts, publishes their sum immediately, looks
-// back for its offset, writes the CSR offsets and expands the runs.
-template <bool kVdb>
-__global__ void __launch_bounds__(kBS) emit_kernel(
+// Exclusive scan of the per-tile sums by one CTA of 1024 threads.  The sums
+// go through shared memory in chunks of 4096 (coalesced loads and stores);
+// each thread scans 4 consecutive entries, a CTA scan joins the threads and
+// a carry joins the chunks.  Writes the total and offsets[n] too.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+
+__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(
+    const int64_t* __restrict__ tile_sum, int64_t T, int64_t* __restrict__ tile_prefix,
+    int64_t* __restrict__ total, int64_t* __restrict__ offsets_end) {
+  __shared__ int64_t buf[kScanThreads * kScanPer];
+  __shared__ int64_t wt[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t carry = 0;
+  for (int64_t c0 = 0; c0 < T; c0 += kScanThreads * kScanPer) {
+    const int64_t m = min((int64_t)kScanThreads * kScanPer, T - c0);
+    for (int i = threadIdx.x; i < kScanThreads * kScanPer; i += kScanThreads)
+      buf[i] = i < m ? tile_sum[c0 + i] : 0;
+    __syncthreads();
+    int64_t v[kScanPer];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      v[j] = buf[threadIdx.x * kScanPer + j];
+      sum += v[j];
+    }
+    int64_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wt[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const int64_t t = wt[lane];
+      int64_t ti = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, ti, o);
+        if (lane >= o) ti += y;
+      }
+      wt[lane] = ti - t;
+      if (lane == 31) wt[32] = ti;
+    }
+    __syncthreads();
+    int64_t run = carry + wt[warp] + inc - sum;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      buf[threadIdx.x * kScanPer + j] = run;
+      run += v[j];
+    }
+    carry += wt[32];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kScanThreads) tile_prefix[c0 + i] = buf[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *total = carry;
+    *offsets_end = carry;
+  }
+}
+
+constexpr int kEmitWarps = 4;
+
+// Pass 2.  One warp per 32-ray tile, independent of every other warp: its
+// offset is the tile's prefix plus a warp scan; its runs go to shared
+// memory and are expanded into samples.
+template <int kMode>
+__global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
-    const uint2* __restrict__ runs, int64_t* __restrict__ offsets,
-    int32_t* __restrict__ ray_idx, float* __restrict__ t0, float* __restrict__ t1,
-    int64_t capacity, unsigned long long* __restrict__ tile_state,
-    unsigned* __restrict__ tile_counter, unsigned* __restrict__ status,
-    int64_t* __restrict__ total_out) {
-  __shared__ uint2 s_runs[kMaxRuns * kBS];  // run j of the CTA's ray i at [j * kBS + i]
-  __shared__ int s_tile;
-  __shared__ int64_t s_prefix;
-  if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
-  __syncthreads();
-  const int tile = s_tile;
-  const int64_t r = (int64_t)tile * kBS + threadIdx.x;
+    const uint2* __restrict__ runs, const int64_t* __restrict__ tile_prefix,
+    int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
+    float* __restrict__ t1, int64_t capacity, unsigned* __restrict__ status) {
+  __shared__ uint2 s_runs[kEmitWarps][kMaxRuns * 32];  // run j of lane i at [j * 32 + i]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tile = (int64_t)blockIdx.x * kEmitWarps + warp;
+  if (tile * 32 >= n) return;  // uniform per warp
+  const int64_t r = tile * 32 + lane;
   const int64_t c = r < n ? (int64_t)counts[r] : 0;
   const int nr = r < n ? (int)nruns[r] : 0;
-  if (capacity > 0) {  // runs to shared memory first (their loads overlap the look-back)
+  uint2* my_runs = s_runs[warp];
+  if (capacity > 0) {
     const int kept = min(nr, kMaxRuns);
     for (int j = 0; __any_sync(kFull, j < kept); ++j)
-      if (j < kept) s_runs[j * kBS + threadIdx.x] = __ldg(runs + (int64_t)j * n + r);
+      if (j < kept) my_runs[j * 32 + lane] = __ldg(runs + (int64_t)j * n + r);
+    __syncwarp();
   }
-  int64_t agg = 0;
-  const int64_t local = cta_exclusive_scan64(c, &agg);
-  if (threadIdx.x < 32) {
-    const int64_t pre = lookback(tile_state, tile, agg, status);
-    if (threadIdx.x == 0) s_prefix = pre;
+  int64_t inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
   }
-  __syncthreads();
-  const int64_t off = s_prefix + local;
+  const int64_t off = __ldg(tile_prefix + tile) + inc - c;
   if (r < n) offsets[r] = off;
-  if (tile == (int)gridDim.x - 1 && threadIdx.x == kBS - 1) {
-    offsets[n] = off + c;
-    *total_out = off + c;
-  }
   if (capacity <= 0) return;
-  const int warp = threadIdx.x >> 5;
-  const int64_t r0 = (int64_t)tile * kBS + warp * 32;
   const bool overflow = nr > kMaxRuns;
-  expand_warp<true>(off, c, overflow, s_runs + warp * 32, kBS, (int32_t)r0, lat.t, capacity,
-                    ray_idx, t0, t1);
+  expand_warp<true>(off, c, overflow, my_runs, 32, (int32_t)(tile * 32), lat.t, capacity, ray_idx,
+                    t0, t1);
   if (overflow) {
     Ray ray;
     load_ray(ro, rd, r, ray);
     const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
     int unused = 0;
-    walk<kVdb, true, false>(g, global_tabs(g), lat, h, ray, nullptr, 0, unused, (int32_t)r, off,
-                            capacity, ray_idx, t0, t1, status);
+    walk<kMode, true, false>(g, global_tabs(g), lat, h, ray, nullptr, 0, unused, (int32_t)r, off,
+                             capacity, ray_idx, t0, t1, status);
   }
 }
 
@@ -910,9 +1023,14 @@ int finish(int64_t* hw, const char* header, int64_t capacity, int64_t* total_out
   return HDDA_OK;
 }
 
+int walk_mode(const hdda_grid* grid) {
+  if (grid->kind == HDDA_GRID_DENSE) return kModeDense;
+  return grid->refine ? kModeVdbRefined : kModeVdb;
+}
+
 // One-pass launch over scratch = [32-byte header | tile states]:
 // header = {tile counter u32, status u32, total i64}.
-int run_onepass(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+int run_onepass(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
                 const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
                 int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
                 cudaStream_t s) {
@@ -923,29 +1041,51 @@ int run_onepass(bool vdb, const float* ro, const float* rd, int64_t n, const hdd
   unsigned long long* state = reinterpret_cast<unsigned long long*>(scratch + 32);
   HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 32 + 8 * (size_t)nb, s));
   const GridDev g = grid->view();
-  if (vdb)
-    onepass_kernel<true><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0, t1,
-                                            capacity, state, counter, status, total);
-  else
-    onepass_kernel<false><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0, t1,
-                                             capacity, state, counter, status, total);
+  switch (walk_mode(grid)) {
+    case kModeDense:
+      onepass_kernel<kModeDense><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0, t1,
+                                                    capacity, state, counter, status, total);
+      break;
+    case kModeVdb:
+      onepass_kernel<kModeVdb><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0, t1,
+                                                  capacity, state, counter, status, total);
+      break;
+    default:
+      onepass_kernel<kModeVdbRefined><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0,
+                                                         t1, capacity, state, counter, status,
+                                                         total);
+      break;
+  }
   HDDA_CUDA_TRY(cudaGetLastError());
   return finish(hw, scratch, capacity, total_out, s);
 }
 
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 // Bytes of the two-pass scratch for n rays.
 size_t twopass_scratch_bytes(int64_t n) {
-  const int64_t nb = (n + kBS - 1) / kBS;
-  auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  return 256 + a(8 * (size_t)nb) + a(4 * (size_t)n) + a((size_t)n) +
-         a(sizeof(uint2) * kMaxRuns * (size_t)n);
+  const int64_t T = (n + 31) / 32;
+  return 256 + 2 * a256(8 * (size_t)T) + a256(4 * (size_t)n) + a256((size_t)n) +
+         a256(sizeof(uint2) * kMaxRuns * (size_t)n);
 }
 
-template <bool kVdb, bool kSm>
-int launch_walk(const float* ro, const float* rd, int64_t n, const GridDev& g,
-                const LatticeDev& lat, size_t smem, int32_t* counts, uint8_t* nruns, uint2* runs,
-                unsigned* counter, unsigned* status, cudaStream_t s) {
-  auto kern = walk_kernel<kVdb, kSm>;
+struct WalkArgs {
+  const float* ro;
+  const float* rd;
+  int64_t n;
+  GridDev g;
+  LatticeDev lat;
+  int32_t* counts;
+  uint8_t* nruns;
+  uint2* runs;
+  int64_t* tile_sum;
+  unsigned* counter;
+  unsigned* status;
+};
+
+template <int kMode, bool kSm>
+int launch_walk(const WalkArgs& w, size_t smem, cudaStream_t s) {
+  auto kern = walk_kernel<kMode, kSm>;
   if (smem > 48 * 1024)
     HDDA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
@@ -953,64 +1093,86 @@ int launch_walk(const float* ro, const float* rd, int64_t n, const GridDev& g,
   HDDA_CUDA_TRY(cudaGetDevice(&dev));
   HDDA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HDDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkBS, smem));
-  const int64_t want = (n + kWalkBS - 1) / kWalkBS;
+  const int64_t want = (w.n + kWalkBS - 1) / kWalkBS;
   const int64_t full = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   const unsigned grid = (unsigned)(want < full ? want : full);
-  kern<<<grid, kWalkBS, smem, s>>>(ro, rd, n, g, lat, counts, nruns, runs, counter, status);
+  kern<<<grid, kWalkBS, smem, s>>>(w.ro, w.rd, w.n, w.g, w.lat, w.counts, w.nruns, w.runs,
+                                   w.tile_sum, w.counter, w.status);
   HDDA_CUDA_TRY(cudaGetLastError());
   return HDDA_OK;
 }
 
+template <int kMode>
+int launch_walk_mode(const WalkArgs& w, size_t stage_bytes, cudaStream_t s) {
+  return stage_bytes <= kMaxStageBytes ? launch_walk<kMode, true>(w, stage_bytes, s)
+                                       : launch_walk<kMode, false>(w, 0, s);
+}
+
+const char* walk_name(int mode) {
+  return mode == kModeDense ? "dense_walk" : mode == kModeVdb ? "hdda_walk_plain" : "hdda_walk";
+}
+const char* emit_name(int mode) {
+  return mode == kModeDense ? "dense_emit" : mode == kModeVdb ? "hdda_emit_plain" : "hdda_emit";
+}
+
 // Two-pass launch.  Scratch: [0, 256) header {walk counter u32, status u32,
-// total i64, emit counter u32}, then tile states, counts, run counts, runs.
-int run_twopass(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+// total i64}, then tile sums, tile prefixes, counts, run counts, runs.
+int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
                 const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
                 int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
                 cudaStream_t s) {
-  const int64_t nb = (n + kBS - 1) / kBS;
-  auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int64_t T = (n + 31) / 32;
   unsigned* walk_counter = reinterpret_cast<unsigned*>(scratch);
   unsigned* status = walk_counter + 1;
   int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
-  unsigned* emit_counter = reinterpret_cast<unsigned*>(scratch + 16);
   char* p = scratch + 256;
-  unsigned long long* state = reinterpret_cast<unsigned long long*>(p);
-  p += a(8 * (size_t)nb);
+  int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
+  p += a256(8 * (size_t)T);
+  int64_t* tile_prefix = reinterpret_cast<int64_t*>(p);
+  p += a256(8 * (size_t)T);
   int32_t* counts = reinterpret_cast<int32_t*>(p);
-  p += a(4 * (size_t)n);
+  p += a256(4 * (size_t)n);
   uint8_t* nruns = reinterpret_cast<uint8_t*>(p);
-  p += a((size_t)n);
+  p += a256((size_t)n);
   uint2* runs = reinterpret_cast<uint2*>(p);
-  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256 + 8 * (size_t)nb, s));
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
 
-  const GridDev g = grid->view();
-  const StageLayout sl = stage_layout(lat.K, g.L, g.R, grid->nodes_total(), vdb);
-  const bool staged = sl.bytes <= kMaxStageBytes;
+  const int mode = walk_mode(grid);
+  const WalkArgs w{ro, rd, n, grid->view(), lat, counts, nruns, runs, tile_sum, walk_counter,
+                   status};
+  const size_t stage = stage_layout(lat.K, w.g.L, w.g.R, grid->nodes_total(), mode).bytes;
   {
-    KernelTimer kt(vdb ? "hdda_walk" : "dense_walk", s);
-    int st;
-    if (vdb)
-      st = staged ? launch_walk<true, true>(ro, rd, n, g, lat, sl.bytes, counts, nruns, runs,
-                                            walk_counter, status, s)
-                  : launch_walk<true, false>(ro, rd, n, g, lat, 0, counts, nruns, runs,
-                                             walk_counter, status, s);
-    else
-      st = staged ? launch_walk<false, true>(ro, rd, n, g, lat, sl.bytes, counts, nruns, runs,
-                                             walk_counter, status, s)
-                  : launch_walk<false, false>(ro, rd, n, g, lat, 0, counts, nruns, runs,
-                                              walk_counter, status, s);
+    KernelTimer kt(walk_name(mode), s);
+    const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, s)
+                   : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, s)
+                                      : launch_walk_mode<kModeVdbRefined>(w, stage, s);
     if (st != HDDA_OK) return st;
   }
   {
-    KernelTimer kt(vdb ? "hdda_emit" : "dense_emit", s);
-    if (vdb)
-      emit_kernel<true><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, counts, nruns, runs,
-                                                     offsets, ray_idx, t0, t1, capacity, state,
-                                                     emit_counter, status, total);
-    else
-      emit_kernel<false><<<(unsigned)nb, kBS, 0, s>>>(ro, rd, n, g, lat, counts, nruns, runs,
-                                                      offsets, ray_idx, t0, t1, capacity, state,
-                                                      emit_counter, status, total);
+    KernelTimer kt("tile_scan", s);
+    tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_sum, T, tile_prefix, total, offsets + n);
+  }
+  HDDA_CUDA_TRY(cudaGetLastError());
+  {
+    KernelTimer kt(emit_name(mode), s);
+    const unsigned nb = (unsigned)((T + kEmitWarps - 1) / kEmitWarps);
+    switch (mode) {
+      case kModeDense:
+        emit_kernel<kModeDense><<<nb, kEmitWarps * 32, 0, s>>>(
+            ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
+            capacity, status);
+        break;
+      case kModeVdb:
+        emit_kernel<kModeVdb><<<nb, kEmitWarps * 32, 0, s>>>(
+            ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
+            capacity, status);
+        break;
+      default:
+        emit_kernel<kModeVdbRefined><<<nb, kEmitWarps * 32, 0, s>>>(
+            ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
+            capacity, status);
+        break;
+    }
   }
   HDDA_CUDA_TRY(cudaGetLastError());
   return finish(hw, scratch, capacity, total_out, s);
@@ -1036,8 +1198,8 @@ int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_g
   if (st != HDDA_OK) return st;
   char* scratch = nullptr;
   HDDA_CUDA_TRY(cudaMallocAsync(&scratch, twopass_scratch_bytes(n), s));
-  st = run_twopass(vdb, ro, rd, n, grid, lat, offsets, ray_idx, t0, t1, capacity, total_out,
-                   scratch, hw, s);
+  st = run_twopass(ro, rd, n, grid, lat, offsets, ray_idx, t0, t1, capacity, total_out, scratch,
+                   hw, s);
   cudaError_t e = cudaFreeAsync(scratch, s);
   if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
   return st;
@@ -1100,8 +1262,8 @@ int traverse_with_scratch(bool vdb, const float* ro, const float* rd, int64_t n,
     HDDA_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
     return HDDA_OK;
   }
-  return run_onepass(vdb, ro, rd, n, grid, lattice_view(block, max_k, K), offsets, ray_idx, t0,
-                     t1, capacity, total_out, sampler_scratch, hw, s);
+  return run_onepass(ro, rd, n, grid, lattice_view(block, max_k, K), offsets, ray_idx, t0, t1,
+                     capacity, total_out, sampler_scratch, hw, s);
 }
 
 }  // namespace hdda

@@ -20,13 +20,14 @@ from . import build as _build
 OK = 0
 ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_STEP_LIMIT, ERR_TIMEOUT, ERR_OOM, ERR_INTERNAL = range(1, 8)
 GRID_DENSE, GRID_VDB = 0, 1
-ARRAY_THRESHOLDS, ARRAY_DENSE_BITS, ARRAY_CHILD_MASK, ARRAY_TILE_MASK, ARRAY_LEAF_PREFIX, ARRAY_LEAVES = range(6)
+(ARRAY_THRESHOLDS, ARRAY_DENSE_BITS, ARRAY_CHILD_MASK, ARRAY_TILE_MASK, ARRAY_LEAF_PREFIX,
+ ARRAY_LEAVES, ARRAY_NODE_SUPER, ARRAY_LEAF_SUB) = range(8)
 
 EXPORTED = [
     "hdda_version", "hdda_last_error", "hdda_pack_dense", "hdda_build_vdb", "hdda_grid_rebuild",
     "hdda_grid_stats_get", "hdda_grid_copy_array", "hdda_grid_free", "hdda_traverse_dense",
     "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
-    "hdda_traverse_hdda_noalloc",
+    "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine",
 ]
 
 
@@ -84,6 +85,7 @@ def load(path: str | None = None):
     lib.hdda_grid_rebuild.argtypes = [vp, vp, vp]
     lib.hdda_grid_stats_get.argtypes = [vp, ctypes.POINTER(GridStats)]
     lib.hdda_grid_copy_array.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
+    lib.hdda_grid_set_refine.argtypes = [vp, i32]
     lib.hdda_grid_free.argtypes = [vp]
     lib.hdda_grid_free.restype = None
     trav = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp]
@@ -164,6 +166,10 @@ class Grid:
         _check(load().hdda_grid_copy_array(self._h, which, out.ctypes.data_as(ctypes.c_void_p),
                                            out.nbytes, ctypes.byref(need)))
         return out
+
+    def set_refine(self, on: bool):
+        """VDB grids: walk with (True, default) or without the refinement masks."""
+        _check(load().hdda_grid_set_refine(self._h, 1 if on else 0))
 
     def rebuild(self, dense: torch.Tensor, stream=None):
         d = _cuda(dense, torch.uint8)

@@ -44,6 +44,9 @@ def check_all(H, occ, aabbs, o, d, p, what):
     vdb = gpu_samples(H, "hdda", ot, dt, gv, prm)
     assert_same(dense, ref, what + " dense-DDA vs oracle")
     assert_same(vdb, ref, what + " HDDA vs oracle")
+    gv.set_refine(False)
+    plain = gpu_samples(H, "hdda", ot, dt, gv, prm)
+    assert_same(plain, ref, what + " HDDA without refinement vs oracle")
     return ref
 
 
@@ -143,6 +146,9 @@ def _full_vs_subset(H, sc, o, d, stride, what):
     dense = gpu_samples(H, "dense", ot, dt, gd, prm)
     vdb = gpu_samples(H, "hdda", ot, dt, gv, prm)
     assert_same(dense, vdb, what + " full frame: dense-DDA vs HDDA")
+    gv.set_refine(False)
+    assert_same(gpu_samples(H, "hdda", ot, dt, gv, prm), vdb, what + " full frame: plain vs refined")
+    gv.set_refine(True)
     # oracle on a stratified subset of the same launch's rays
     so, sd, sel = subset_rays(o, d, stride, offset=stride // 3)
     ref = oracle_samples(so, sd, sc.occ, sc.aabbs, sc.params)
@@ -185,6 +191,9 @@ def test_grid_structures_match_oracle(H):
     st = gv.stats()
     assert st.n_leaves == v["n_leaves"] and st.n_tiles == v["n_tiles"]
     assert st.dense_bytes == 3 * oracle.dense_words_per_level(37) * 4
+    nsuper, lsub = oracle.vdb_refinement(v)
+    np.testing.assert_array_equal(gv.array(H.ARRAY_NODE_SUPER), nsuper.reshape(-1))
+    np.testing.assert_array_equal(gv.array(H.ARRAY_LEAF_SUB), lsub.reshape(-1))
     # leaf prefix: global index of the first leaf of each child-mask word
     child = v["child"].reshape(-1)
     pc = np.array([bin(int(w)).count("1") for w in child])
@@ -217,7 +226,11 @@ def test_table3_sizes(H):
     st = gv.stats()
     v = oracle.build_vdb(sc.occ)
     assert st.n_leaves == v["n_leaves"] and st.n_tiles == v["n_tiles"]
-    assert st.bytes == 36 + 3 * 129 * 4 + (3 * 128 * 4 + 4) + 64 * v["n_leaves"]
+    # level table + thresholds + node masks + leaves + refinement masks (node and leaf)
+    assert st.bytes == (36 + 3 * 129 * 4 + (3 * 128 * 4 + 4) + 64 * v["n_leaves"]
+                        + 18 * 4 + 12 * v["n_leaves"])
+    gv.set_refine(False)
+    assert gv.stats().bytes == 36 + 3 * 129 * 4 + (3 * 128 * 4 + 4) + 64 * v["n_leaves"]
 
 
 def test_rebuild_matches_fresh_build(H):

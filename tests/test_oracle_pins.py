@@ -317,3 +317,17 @@ def test_vdb_round_trip_and_counts(res, p):
     assert v["n_leaves"] == partial and v["n_tiles"] == full
     # tile and child bits never overlap
     assert not np.any(v["child"] & v["tile"])
+
+
+def test_vdb_refinement_masks_single_voxel():
+    # voxel (5, 9, 40) of a 64^3 grid: 32^3 group (0, 0, 1) -> bit 1 of word 0; 16^3 group
+    # (0, 0, 2) -> bit 2 of word 2; in its leaf, local (5, 1, 0): 2^3 cell (2, 0, 0) -> bit 32,
+    # i.e. bit 0 of word 1; 4^3 cell (1, 0, 0) -> bit 4 of word 2
+    occ = np.zeros((1, 64, 64, 64), np.uint8)
+    occ[0, 5, 9, 40] = 1
+    v = oracle.build_vdb(occ)
+    ns, ls = oracle.vdb_refinement(v)
+    assert ns.shape == (1, 1, 18)
+    assert ns[0, 0, 0] == 1 << 1 and ns[0, 0, 1] == 0
+    assert ns[0, 0, 2] == 1 << 2 and not ns[0, 0, 3:].any()
+    assert ls.tolist() == [[0, 1, 1 << 4]]
