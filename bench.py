@@ -40,6 +40,9 @@ L2_FLUSH_BYTES = 256 << 20
 # 1 add (density), 3 fma (colour); the exp2 runs on the MUFU pipe alongside.
 COMPOSITE_FP32_PER_BLOB = 12
 KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
+# DRAM bytes (read + write) per launch from ncu --set full of the object-centric step, for the
+# roofline's "traffic"; an entry must be dropped whenever its kernel changes.
+PROFILED_TRAFFIC = {"composite": 238_345_472}
 
 
 def parse_args():
@@ -306,11 +309,13 @@ def run_ours(args):
             ach = alg_inst[name] / (avg / 1e3) / 1e12
             return {"kernel": name, "bound": "alu", "achieved": round(ach, 2),
                     "peak": round(alu_peak, 2), "unit": "Tinst/s (FP32 pipe)",
-                    "frac": round(ach / alu_peak, 4), "traffic": None,
+                    "frac": round(ach / alu_peak, 4), "traffic": PROFILED_TRAFFIC.get(name),
+                    "alg_bytes": int(alg_bytes.get(name, 0)),
                     "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock"}
         ach = alg_bytes.get(name, 0) / (avg / 1e3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
-                "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                "traffic": PROFILED_TRAFFIC.get(name),
                 "peak_source": peak_src}
 
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
