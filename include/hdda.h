@@ -275,6 +275,64 @@ int hdda_traverse_hdda_noalloc(const float* rays_o, const float* rays_d, int64_t
                                int64_t capacity, int64_t* total_out, hdda_stream_t stream);
 
 /*
+ * Batched sampling: many traversal jobs in one launch sequence.
+ *
+ * Each job is one traversal with its own rays, grid, lattice parameters and
+ * output buffers (the fields mean what the arguments of hdda_traverse_hdda
+ * mean; a job's `capacity` may be 0 to count only).  All grids of a batch
+ * must be of one kind (dense, VDB, or VDB with refinement off).  The jobs'
+ * rays are cut into 32-ray tiles numbered over the whole batch; persistent
+ * warps take tiles from one counter (work stealing across jobs), so jobs of
+ * very different sizes share the GPU without a launch per job.  A batch is
+ * a plan: hdda_batch_create fixes the job table and scratch (and, with
+ * use_graph, captures the launch sequence into a CUDA graph); every
+ * hdda_batch_launch re-runs it, reading whatever the job buffers then hold.
+ * Buffers and grids must stay alive and unchanged in shape while the batch
+ * exists.  Not in the paper (its renderer draws one frame at a time); this is
+ * the throughput path for many cameras and scenes.
+ */
+typedef struct {
+    const float* rays_o;     /* device float [n_rays][3]                    */
+    const float* rays_d;     /* device float [n_rays][3]                    */
+    int64_t n_rays;
+    const hdda_grid* grid;
+    hdda_params params;
+    int64_t* offsets;        /* device int64 [n_rays + 1]                  */
+    int32_t* ray_idx;        /* device [capacity]                          */
+    float* t0;
+    float* t1;
+    int64_t capacity;
+} hdda_job;
+
+typedef struct {
+    int walk_block;      /* threads per CTA of the walk: 128, 256 or 512     */
+    int rays_per_fetch;  /* rays a warp takes per atomic fetch: 32..1024, x32 */
+    int emit_warps;      /* warps (32-ray tiles) per CTA of the emit: 2, 4, 8 */
+    int use_graph;       /* capture the sequence in a CUDA graph at create    */
+} hdda_batch_config;
+
+typedef struct hdda_batch hdda_batch;  /* opaque, library-owned */
+
+/* Builds a batch plan for `n_jobs` jobs (HOST array, 1..4096); cfg (HOST) may
+ * be NULL for {256, 64, 4, 1}.  Looks up each job's lattice (synchronising
+ * once per new parameter set) and synchronises the stream once. */
+int hdda_batch_create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg,
+                      hdda_batch** out, hdda_stream_t stream);
+
+/* Runs the batch on `stream` (one graph launch, or its kernels); async. */
+int hdda_batch_launch(hdda_batch* batch, hdda_stream_t stream);
+
+/* Waits for the stream and reads every job's sample total and status (HOST
+ * arrays of n_jobs; either may be NULL).  A job whose capacity is below its
+ * total gets HDDA_ERR_CAPACITY (its samples below capacity are written) and
+ * the call returns that code too. */
+int hdda_batch_results(hdda_batch* batch, int64_t* totals, uint32_t* status,
+                       hdda_stream_t stream);
+
+/* Frees a batch (waits for the device).  NULL is a no-op. */
+void hdda_batch_free(hdda_batch* batch);
+
+/*
  * Front-to-back compositing of the kept intervals over a Gaussian-blob field
  * (Sec. 1: densities and colours of the sampled points are accumulated into
  * the pixel).  For each ray, in order of its samples, with x the position at

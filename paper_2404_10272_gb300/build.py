@@ -28,6 +28,7 @@ SOURCES = {
     "traverse.cu": ["-fmad=false"],
     "composite.cu": [],
     "noalloc.cu": [],
+    "batch.cu": ["-fmad=false"],
 }
 
 

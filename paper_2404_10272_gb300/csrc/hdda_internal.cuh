@@ -132,6 +132,8 @@ class KernelTimer {
 // traverse_scratch_bytes(max_k, max_tiles) bytes, 256-byte aligned; nothing
 // is allocated.  Rays per tile: traverse_rays_per_tile().
 size_t traverse_scratch_bytes(int max_k, int64_t max_tiles);
+// Validates params and returns the cached device lattice for them (traverse.cu).
+int lattice_for(const hdda_params* p, cudaStream_t s, LatticeDev* out);
 int64_t traverse_rays_per_tile();
 int traverse_with_scratch(bool vdb, const float* ro, const float* rd, int64_t n,
                           const struct ::hdda_grid* grid, const hdda_params* params,

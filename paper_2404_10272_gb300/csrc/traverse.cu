@@ -46,32 +46,13 @@
 #include <mutex>
 #include <vector>
 
-#include "grid.cuh"
+#include "walk.cuh"
 
 namespace hdda {
 namespace {
 
 constexpr int kBS = 128;        // rays (threads) per CTA tile
-constexpr int kMaxRuns = 16;    // runs per ray kept in shared memory
-constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kSpinLimit = 1u << 22;  // look-back polls before giving up
-
-// Loads from a table that lives in shared memory (kSm) or in global memory
-// (read-only path).
-template <bool kSm, typename T>
-__device__ __forceinline__ T ld(const T* p) {
-  if constexpr (kSm) return *p;
-  else return __ldg(p);
-}
-
-// ---------------------------------------------------------------------------
-// lattice
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float lattice_next(float t, const hdda_params& p) {
-  const float dt = fminf(fmaxf(__fmul_rn(t, p.cone_angle), p.step), p.max_step);
-  return __fadd_rn(t, dt);
-}
 
 __global__ void lattice_count_kernel(hdda_params p, int64_t* out) {
   float t = p.near_t;
@@ -122,359 +103,6 @@ __global__ void lattice_fill_kernel(hdda_params p, int K, int max_k, char* __res
   hdr[0] = key0;
   hdr[1] = shift;
   hdr[2] = (uint32_t)NB;
-}
-
-LatticeDev lattice_view(char* block, int max_k, int K) {
-  float* t = reinterpret_cast<float*>(block);
-  float* tm = t + max_k + 1;
-  int* kidx = reinterpret_cast<int*>(tm + max_k);
-  uint32_t* hdr = reinterpret_cast<uint32_t*>(kidx + kKidxMax + 2);
-  return LatticeDev{t, tm, kidx, hdr, K};
-}
-
-struct LatHdr {
-  uint32_t key0, shift;
-  int NB;
-};
-
-// First k with tm_k >= te (K if none), through the bucket index.
-template <bool kSm>
-__device__ __forceinline__ int first_k_at(const LatticeDev& lat, const LatHdr& h, float te) {
-  const uint32_t key = float_key(te);
-  const int b = key < h.key0 ? 0 : (int)min((key - h.key0) >> h.shift, (uint32_t)h.NB);
-  int lo = ld<kSm>(lat.kidx + b);
-  const int hi = ld<kSm>(lat.kidx + b + 1);
-  while (lo < hi && ld<kSm>(lat.tm + lo) < te) ++lo;
-  return lo;
-}
-
-// ---------------------------------------------------------------------------
-// the walk
-// ---------------------------------------------------------------------------
-
-struct Ray {
-  float o[3], d[3], inv[3];
-  bool neg[3];  // direction component < 0 (a zero component counts as positive)
-};
-
-__device__ __forceinline__ bool load_ray(const float* __restrict__ ro,
-                                         const float* __restrict__ rd, int64_t r, Ray& ray) {
-  bool ok = true;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    ray.o[c] = __ldg(ro + 3 * r + c);
-    ray.d[c] = __ldg(rd + 3 * r + c);
-    ok &= isfinite(ray.o[c]) && isfinite(ray.d[c]);
-    ray.neg[c] = ray.d[c] < 0.f;
-    ray.inv[c] = 1.0f / ray.d[c];  // estimates only
-  }
-  return ok;
-}
-
-// The grid tables the walk reads per region, in shared memory (staged) or
-// global memory; the rest of the grid stays in the GridDev kernel parameter.
-struct Tabs {
-  const float* thr;
-  const uint32_t* child;
-  const uint32_t* tile;
-  const uint32_t* prefix;
-  const uint32_t* nstate;
-  const uint32_t* nsuper;
-};
-
-__device__ __forceinline__ Tabs global_tabs(const GridDev& g) {
-  return Tabs{g.thr, g.child, g.tile, g.prefix, g.nstate, g.nsuper};
-}
-
-// x = o + tm * d per axis, one rounding per operation.
-__device__ __forceinline__ void point_at(const Ray& r, float tm, float x[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) x[c] = __fadd_rn(r.o[c], __fmul_rn(tm, r.d[c]));
-}
-
-// A region is kept as one exit plane per axis: e[c] bounds the region on the
-// side the ray moves towards (upper bound, exclusive, for d >= 0; lower
-// bound, inclusive, for d < 0).
-__device__ __forceinline__ bool outside(const float x[3], const float e[3], const Ray& r) {
-  return ((x[0] >= e[0]) != r.neg[0]) | ((x[1] >= e[1]) != r.neg[1]) |
-         ((x[2] >= e[2]) != r.neg[2]);
-}
-
-// Intersects the region with [lo, hi) along axis c.
-__device__ __forceinline__ void clip(float e[3], const Ray& r, int c, float lo, float hi) {
-  e[c] = r.neg[c] ? fmaxf(e[c], lo) : fminf(e[c], hi);
-}
-
-// Intersects the region with voxels [a0, a1) of axis c of one level, using
-// the exact thresholds X[a] (only the bound on the exit side is loaded).
-template <bool kSm>
-__device__ __forceinline__ void clip_cells(float e[3], const Ray& r, const float* thr, int R1,
-                                           int c, int a0, int a1) {
-  if (r.neg[c]) e[c] = fmaxf(e[c], ld<kSm>(thr + c * R1 + a0));
-  else e[c] = fminf(e[c], ld<kSm>(thr + c * R1 + a1));
-}
-
-// Classifies x and sets e to the region holding it.  Returns its occupancy.
-// kSm: the tables in tb point into shared memory.
-template <int kMode, bool kSm>
-__device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const Ray& r,
-                                       const float x[3], float e[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) e[c] = r.neg[c] ? -INFINITY : INFINITY;
-  int l = -1;
-  for (int lv = 0; lv < g.L; ++lv) {
-    const LevelDev& B = g.lv[lv];
-    bool inside = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) inside &= (x[c] >= B.lo[c]) & (x[c] < B.hi[c]);
-    if (inside) { l = lv; break; }
-    // x lies outside this (finer) box: keep a half-space that separates the
-    // ray's later points from it, preferring the one it leaves last.
-    int best = -1;
-    float best_t = -1.f;
-    bool never = false;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (x[c] < B.lo[c]) {
-        if (!(r.d[c] > 0.f)) never = true;  // coordinate never grows: never enters
-        else {
-          const float t = (B.lo[c] - x[c]) * r.inv[c];
-          if (t > best_t) { best_t = t; best = c; }
-        }
-      } else if (x[c] >= B.hi[c]) {
-        if (!(r.d[c] < 0.f)) never = true;
-        else {
-          const float t = (B.hi[c] - x[c]) * r.inv[c];
-          if (t > best_t) { best_t = t; best = c; }
-        }
-      }
-    }
-    if (never || best < 0) continue;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (c != best) continue;
-      if (r.neg[c]) e[c] = fmaxf(e[c], B.hi[c]);  // region x >= hi
-      else e[c] = fminf(e[c], B.lo[c]);           // region x < lo
-    }
-  }
-  if (l < 0) return false;
-
-  const LevelDev& V = g.lv[l];
-  int i[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    clip(e, r, c, V.lo[c], V.hi[c]);
-    i[c] = voxel_index(x[c], V.lo[c], V.s[c], g.R);
-  }
-  const int R1 = g.R + 1;
-  const float* thr = tb.thr + (int64_t)l * 3 * R1;
-  if constexpr (kMode == kModeDense) {
-    const int64_t lin = ((int64_t)i[0] * g.R + i[1]) * g.R + i[2];
-    const uint32_t w = __ldg(g.bits + (int64_t)l * g.W + (lin >> 5));
-#pragma unroll
-    for (int c = 0; c < 3; ++c) clip_cells<kSm>(e, r, thr, R1, c, i[c], i[c] + 1);
-    return (w >> (lin & 31)) & 1u;
-  }
-  // node level
-  const int N = g.N;
-  const int64_t ng = (int64_t)l * N * N * N +
-                     ((i[0] >> 7) * N + (i[1] >> 7)) * N + (i[2] >> 7);
-  const uint32_t st = ld<kSm>(tb.nstate + ng);
-  if (st != kNodeMixed) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int a0 = i[c] & ~(kNodeVox - 1);
-      clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + kNodeVox, g.R));
-    }
-    return st == kNodeFull;
-  }
-  if constexpr (kMode == kModeVdbRefined) {
-    // empty 32^3 group, then empty 16^3 group of the node
-    const uint32_t* ns = tb.nsuper + ng * kSuperWords;
-    const int g4 = (((i[0] >> 5) & 3) * 4 + ((i[1] >> 5) & 3)) * 4 + ((i[2] >> 5) & 3);
-    if (!((ld<kSm>(ns + (g4 >> 5)) >> (g4 & 31)) & 1u)) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int a0 = i[c] & ~31;
-        clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 32, g.R));
-      }
-      return false;
-    }
-    const int g2 = (((i[0] >> 4) & 7) * 8 + ((i[1] >> 4) & 7)) * 8 + ((i[2] >> 4) & 7);
-    if (!((ld<kSm>(ns + 2 + (g2 >> 5)) >> (g2 & 31)) & 1u)) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int a0 = i[c] & ~15;
-        clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 16, g.R));
-      }
-      return false;
-    }
-  }
-  // block level: empty or tile
-  const int cell = (((i[0] >> 3) & 15) * 16 + ((i[1] >> 3) & 15)) * 16 + ((i[2] >> 3) & 15);
-  const int w = cell >> 5;
-  const uint32_t bit = 1u << (cell & 31);
-  const uint32_t cw = ld<kSm>(tb.child + ng * kNodeWords + w);
-  if (!(cw & bit)) {
-    const uint32_t tw = ld<kSm>(tb.tile + ng * kNodeWords + w);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int a0 = i[c] & ~(kBlockDim - 1);
-      clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + kBlockDim, g.R));
-    }
-    return (tw & bit) != 0u;
-  }
-  // voxel of a leaf
-  const uint32_t leaf = ld<kSm>(tb.prefix + ng * kNodeWords + w) + __popc(cw & (bit - 1u));
-  if constexpr (kMode == kModeVdbRefined) {
-    // empty 4^3 cell, then empty 2^3 cell of the leaf
-    const uint32_t* ls = g.lsub + (int64_t)leaf * kLeafSubWords;
-    const int c4 = (((i[0] >> 2) & 1) * 2 + ((i[1] >> 2) & 1)) * 2 + ((i[2] >> 2) & 1);
-    if (!((__ldg(ls + 2) >> c4) & 1u)) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int a0 = i[c] & ~3;
-        clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 4, g.R));
-      }
-      return false;
-    }
-    const int c2 = (((i[0] >> 1) & 3) * 4 + ((i[1] >> 1) & 3)) * 4 + ((i[2] >> 1) & 3);
-    if (!((__ldg(ls + (c2 >> 5)) >> (c2 & 31)) & 1u)) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int a0 = i[c] & ~1;
-        clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 2, g.R));
-      }
-      return false;
-    }
-  }
-  const int v = ((i[0] & 7) * 8 + (i[1] & 7)) * 8 + (i[2] & 7);
-  const uint32_t lw = __ldg(g.leaves + (int64_t)leaf * kLeafWords + (v >> 5));
-#pragma unroll
-  for (int c = 0; c < 3; ++c) clip_cells<kSm>(e, r, thr, R1, c, i[c], i[c] + 1);
-  return (lw >> (v & 31)) & 1u;
-}
-
-// First k' in (k, K] whose point is outside the region (K if none).  The
-// point of k is inside.  xo receives the point of k' when k' < K.
-template <bool kSm>
-__device__ __forceinline__ int cross(const Ray& r, const LatticeDev& lat, const LatHdr& h, int k,
-                                     const float e[3], float xo[3]) {
-  const int K = lat.K;
-  // estimate: the ray parameter where it meets the first exit plane
-  float te = INFINITY;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    if (r.d[c] != 0.f) te = fminf(te, (e[c] - r.o[c]) * r.inv[c]);
-  int ke = max(first_k_at<kSm>(lat, h, te), k + 1);
-  int lo, hi;  // invariant: point lo inside (lo >= k); point hi outside, or hi == K
-  float xp[3];
-  if (ke >= K) {
-    if (K - 1 == k) return K;
-    point_at(r, ld<kSm>(lat.tm + K - 1), xp);
-    if (!outside(xp, e, r)) return K;
-    lo = k;
-    hi = K - 1;
-    xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
-  } else {
-    point_at(r, ld<kSm>(lat.tm + ke), xp);
-    if (!outside(xp, e, r)) {
-      // estimate too early: gallop forward
-      lo = ke;
-      int step = 1;
-      for (;;) {
-        hi = lo + step;
-        if (hi >= K) { hi = K; break; }
-        point_at(r, ld<kSm>(lat.tm + hi), xp);
-        if (outside(xp, e, r)) {
-          xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
-          break;
-        }
-        lo = hi;
-        step <<= 1;
-      }
-    } else {
-      xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
-      if (ke - 1 == k) return ke;
-      point_at(r, ld<kSm>(lat.tm + ke - 1), xp);
-      if (!outside(xp, e, r)) return ke;  // the usual case: estimate exact
-      lo = k;
-      hi = ke - 1;
-      xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
-    }
-  }
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    point_at(r, ld<kSm>(lat.tm + mid), xp);
-    if (outside(xp, e, r)) {
-      hi = mid;
-      xo[0] = xp[0]; xo[1] = xp[1]; xo[2] = xp[2];
-    } else {
-      lo = mid;
-    }
-  }
-  return hi;
-}
-
-// Walks one ray.  Counts its samples and merges occupied regions into runs
-// [k_begin, k_end): the first kMaxRuns go to runs[j * stride]; nruns counts
-// all.  With kEmit it instead writes the samples from `out`, below
-// `capacity` (lat.t must then be a global-memory table).
-template <int kMode, bool kEmit, bool kSm>
-__device__ __forceinline__ int64_t walk(const GridDev& g, const Tabs& tb, const LatticeDev& lat,
-                                        const LatHdr& h, const Ray& r, uint2* runs,
-                                        int64_t stride, int& nruns, int32_t rid,
-                                        int64_t out, int64_t capacity,
-                                        int32_t* __restrict__ ray_idx, float* __restrict__ t0,
-                                        float* __restrict__ t1, unsigned* __restrict__ status) {
-  const int K = lat.K;
-  int64_t cnt = 0;
-  nruns = 0;
-  if (K <= 0) return 0;
-  int rb = -1, re = -1;  // open run
-  float x[3];
-  point_at(r, ld<kSm>(lat.tm), x);
-  int k = 0;
-  while (k < K) {
-    float e[3];
-    const bool occ = locate<kMode, kSm>(g, tb, r, x, e);
-    if (outside(x, e, r)) atomicOr(status, kDevInternal);  // region must hold its point
-    const int kn = cross<kSm>(r, lat, h, k, e, x);
-    if (occ) {
-      if (kEmit) {
-        float ta = __ldg(lat.t + k);
-        for (int j = k; j < kn; ++j) {
-          const float tb = __ldg(lat.t + j + 1);
-          const int64_t p = out + cnt;
-          if (p < capacity) {
-            ray_idx[p] = rid;
-            t0[p] = ta;
-            t1[p] = tb;
-          }
-          ta = tb;
-          ++cnt;
-        }
-      } else {
-        cnt += kn - k;
-        if (k == re) {
-          re = kn;  // adjacent occupied region: extend the run
-        } else {
-          if (rb >= 0) {
-            if (nruns < kMaxRuns) runs[nruns * stride] = make_uint2(rb, re);
-            ++nruns;
-          }
-          rb = k;
-          re = kn;
-        }
-      }
-    }
-    k = kn;
-  }
-  if (!kEmit && rb >= 0) {
-    if (nruns < kMaxRuns) runs[nruns * stride] = make_uint2(rb, re);
-    ++nruns;
-  }
-  return cnt;
 }
 
 __device__ __forceinline__ int64_t cta_exclusive_scan64(int64_t v, int64_t* total) {
@@ -565,53 +193,6 @@ __device__ int64_t lookback(unsigned long long* state, int tile, int64_t agg,
   }
   if (lane == 0) st_release(state + tile, kFlagPrefix | (unsigned long long)(excl + agg));
   return excl;
-}
-
-// ---------------------------------------------------------------------------
-// expansion of runs into samples
-// ---------------------------------------------------------------------------
-
-// One warp writes the samples of its 32 rays.  Lane i holds ray rid0 + i
-// with `c` samples from output position `off` (rays in order, so the
-// warp's samples are one contiguous range); its runs are runs0[i + j *
-// stride], j < kMaxRuns.  Lane j of each 32-sample chunk finds the ray that
-// owns its position (binary search over the lanes' offsets) and the run
-// inside it.  Rays with more runs than were kept are skipped here; they
-// walk again.  Nothing at or past `capacity` is written.
-template <bool kSm>
-__device__ __forceinline__ void expand_warp(int64_t off, int64_t c, bool overflow,
-                                            const uint2* runs0, int64_t stride, int32_t rid0,
-                                            const float* __restrict__ t, int64_t capacity,
-                                            int32_t* __restrict__ ray_idx,
-                                            float* __restrict__ t0, float* __restrict__ t1) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wbeg = __shfl_sync(kFull, off, 0);
-  const int64_t wend = __shfl_sync(kFull, off + c, 31);
-  for (int64_t base = wbeg; base < wend; base += 32) {
-    const int64_t p = base + lane;
-    int own = 0;  // the last lane whose offset is <= p
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-      const int64_t v = __shfl_sync(kFull, off, own + s);
-      if (v <= p) own += s;
-    }
-    const int64_t own_off = __shfl_sync(kFull, off, own);
-    const int own_ovf = __shfl_sync(kFull, (int)overflow, own);
-    if (p < wend && !own_ovf && p < capacity) {
-      const uint2* rr = runs0 + own;
-      int64_t loc = p - own_off;
-      uint2 run = ld<kSm>(rr);
-      int j = 0;
-      while (loc >= (int64_t)(run.y - run.x)) {
-        loc -= run.y - run.x;
-        run = ld<kSm>(rr + (++j) * stride);
-      }
-      const int k = (int)run.x + (int)loc;
-      ray_idx[p] = rid0 + own;
-      t0[p] = __ldg(t + k);
-      t1[p] = __ldg(t + k + 1);
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -774,69 +355,6 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
     if (lane == 0) tile_sum[tile] = c;
-  }
-}
-
-// Exclusive scan of the per-tile sums by one CTA of 1024 threads.  The sums
-// go through shared memory in chunks of 4096 (coalesced loads and stores);
-// each thread scans 4 consecutive entries, a CTA scan joins the threads and
-// a carry joins the chunks.  Writes the total and offsets[n] too.
-constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 4;
-
-__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(
-    const int64_t* __restrict__ tile_sum, int64_t T, int64_t* __restrict__ tile_prefix,
-    int64_t* __restrict__ total, int64_t* __restrict__ offsets_end) {
-  __shared__ int64_t buf[kScanThreads * kScanPer];
-  __shared__ int64_t wt[33];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t carry = 0;
-  for (int64_t c0 = 0; c0 < T; c0 += kScanThreads * kScanPer) {
-    const int64_t m = min((int64_t)kScanThreads * kScanPer, T - c0);
-    for (int i = threadIdx.x; i < kScanThreads * kScanPer; i += kScanThreads)
-      buf[i] = i < m ? tile_sum[c0 + i] : 0;
-    __syncthreads();
-    int64_t v[kScanPer];
-    int64_t sum = 0;
-#pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-      v[j] = buf[threadIdx.x * kScanPer + j];
-      sum += v[j];
-    }
-    int64_t inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(kFull, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) wt[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-      const int64_t t = wt[lane];
-      int64_t ti = t;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(kFull, ti, o);
-        if (lane >= o) ti += y;
-      }
-      wt[lane] = ti - t;
-      if (lane == 31) wt[32] = ti;
-    }
-    __syncthreads();
-    int64_t run = carry + wt[warp] + inc - sum;
-#pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-      buf[threadIdx.x * kScanPer + j] = run;
-      run += v[j];
-    }
-    carry += wt[32];
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += kScanThreads) tile_prefix[c0 + i] = buf[i];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    *total = carry;
-    *offsets_end = carry;
   }
 }
 
@@ -1206,6 +724,12 @@ int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_g
 }
 
 }  // namespace
+
+int lattice_for(const hdda_params* p, cudaStream_t s, LatticeDev* out) {
+  const int st = validate_params(p);
+  if (st != HDDA_OK) return st;
+  return get_lattice(*p, s, out);
+}
 
 // ---------------------------------------------------------------------------
 // traversal over caller-provided scratch (no allocation of any kind)

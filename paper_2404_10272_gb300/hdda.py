@@ -27,7 +27,8 @@ EXPORTED = [
     "hdda_version", "hdda_last_error", "hdda_pack_dense", "hdda_build_vdb", "hdda_grid_rebuild",
     "hdda_grid_stats_get", "hdda_grid_copy_array", "hdda_grid_free", "hdda_traverse_dense",
     "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
-    "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine",
+    "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine", "hdda_batch_create",
+    "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free",
 ]
 
 
@@ -50,6 +51,18 @@ class Params(ctypes.Structure):
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("rays_o", ctypes.c_void_p), ("rays_d", ctypes.c_void_p), ("n_rays", ctypes.c_int64),
+                ("grid", ctypes.c_void_p), ("params", Params), ("offsets", ctypes.c_void_p),
+                ("ray_idx", ctypes.c_void_p), ("t0", ctypes.c_void_p), ("t1", ctypes.c_void_p),
+                ("capacity", ctypes.c_int64)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("walk_block", ctypes.c_int32), ("rays_per_fetch", ctypes.c_int32),
+                ("emit_warps", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
 class GridStats(ctypes.Structure):
@@ -86,6 +99,12 @@ def load(path: str | None = None):
     lib.hdda_grid_stats_get.argtypes = [vp, ctypes.POINTER(GridStats)]
     lib.hdda_grid_copy_array.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hdda_grid_set_refine.argtypes = [vp, i32]
+    lib.hdda_batch_create.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(BatchConfig),
+                                      ctypes.POINTER(vp), vp]
+    lib.hdda_batch_launch.argtypes = [vp, vp]
+    lib.hdda_batch_results.argtypes = [vp, vp, vp, vp]
+    lib.hdda_batch_free.argtypes = [vp]
+    lib.hdda_batch_free.restype = None
     lib.hdda_grid_free.argtypes = [vp]
     lib.hdda_grid_free.restype = None
     trav = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp]
@@ -96,7 +115,7 @@ def load(path: str | None = None):
     lib.hdda_profiler_enable.argtypes = [i32]
     lib.hdda_profiler_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
     for name in EXPORTED:
-        if name not in ("hdda_version", "hdda_last_error", "hdda_grid_free"):
+        if name not in ("hdda_version", "hdda_last_error", "hdda_grid_free", "hdda_batch_free"):
             getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -313,3 +332,63 @@ def profiler_read() -> dict:
     _check(load().hdda_profiler_read(arr, cap, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
             for i in range(min(n.value, cap))}
+
+
+DEFAULT_BATCH_CONFIG = (256, 64, 4)
+
+
+class Batch:
+    """A batch plan over many traversal jobs (see hdda_batch_create).
+
+    jobs: list of dicts with rays_o, rays_d (CUDA float32 [n, 3]), grid (Grid),
+    params (Params) and out (Samples: offsets [n+1] and sample buffers whose
+    length is the job's capacity).  The tensors and grids are kept alive
+    by the batch.
+    """
+
+    def __init__(self, jobs, config=DEFAULT_BATCH_CONFIG, use_graph=True, stream=None):
+        self._keep = []
+        arr = (Job * len(jobs))()
+        for i, jb in enumerate(jobs):
+            ro = _cuda(jb["rays_o"], torch.float32, (-1, 3))
+            rd = _cuda(jb["rays_d"], torch.float32, (-1, 3))
+            out = jb["out"]
+            self._keep += [ro, rd, out, jb["grid"]]
+            arr[i] = Job(_ptr(ro), _ptr(rd), int(ro.shape[0]), jb["grid"].handle, jb["params"],
+                         _ptr(out.offsets), _ptr(out.ray_idx), _ptr(out.t0), _ptr(out.t1),
+                         int(out.t0.numel()))
+        self.n_jobs = len(jobs)
+        self.jobs = jobs
+        wb, rpf, ew = config
+        cfg = BatchConfig(wb, rpf, ew, 1 if use_graph else 0)
+        self.config = (wb, rpf, ew)
+        h = ctypes.c_void_p()
+        _check(load().hdda_batch_create(arr, self.n_jobs, ctypes.byref(cfg), ctypes.byref(h),
+                                        _stream(stream)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load().hdda_batch_launch(self._h, _stream(stream)))
+
+    def results(self, stream=None, check=True):
+        """(totals, status) per job after the last launch (synchronises)."""
+        totals = (ctypes.c_int64 * self.n_jobs)()
+        status = (ctypes.c_uint32 * self.n_jobs)()
+        code = load().hdda_batch_results(self._h, totals, status, _stream(stream))
+        tot, st = list(totals), list(status)
+        for jb, t in zip(self.jobs, tot):
+            jb["out"].total = t
+        if check:
+            _check(code)
+        return tot, st
+
+    def free(self):
+        if self._h:
+            load().hdda_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -34,7 +34,8 @@ __all__ = [
     "Scene", "Camera", "SamplerParams", "random_rotation", "ellipsoid_occupancy",
     "dilate", "box_occupancy", "cascade_boxes", "look_at_rays", "orbit_camera",
     "gaussian_field", "tiny_scene", "object_scene", "unbounded_scene",
-    "object_cameras", "tiny_camera", "unbounded_camera", "random_grid",
+    "object_cameras", "tiny_camera", "unbounded_camera", "random_grid", "cascade_from",
+    "batch_jobs",
 ]
 
 
@@ -306,3 +307,56 @@ def unbounded_camera(seed: int = 1003, W: int = 1245, H: int = 825, j: int = 0) 
     dirn = rng.normal(size=3)
     dirn /= np.linalg.norm(dirn)
     return Camera(eye=eye, target=eye + dirn, width=W, height=H, fov=1.0)
+
+
+# ---------------------------------------------------------------------------
+# batching workload: many (scene, camera) jobs
+# ---------------------------------------------------------------------------
+
+def cascade_from(base: np.ndarray, levels: int, rng: np.random.Generator, half: float = 1.5):
+    """A cascade whose level 0 is `base` (R^3 over [-half, half)^3) and whose level l covers
+    [-half*2^l, half*2^l)^3: its central half holds the 2x OR-pooled level l-1 (as a trained
+    cascade would) and its outer shell a few random boxes."""
+    R = base.shape[0]
+    occ = np.zeros((levels, R, R, R), np.uint8)
+    occ[0] = base
+    aabbs = cascade_boxes(levels, half)
+    for l in range(1, levels):
+        pooled = occ[l - 1].reshape(R // 2, 2, R // 2, 2, R // 2, 2).max(axis=(1, 3, 5))
+        q = R // 4
+        occ[l, q:q + R // 2, q:q + R // 2, q:q + R // 2] = pooled
+        h, hin = aabbs[l, 3], aabbs[l - 1, 3]
+        boxes = []
+        while len(boxes) < 12:
+            ctr = rng.uniform(-h, h, size=3)
+            if np.all(np.abs(ctr) < hin):
+                continue
+            ext = rng.uniform(0.03, 0.1, size=3) * h
+            boxes.append((ctr - ext, ctr + ext))
+        occ[l] |= box_occupancy(R, aabbs[l, :3], aabbs[l, 3:], boxes)
+    return occ, aabbs
+
+
+def batch_jobs(seed: int = 1004, n: int = 64, min_side: int = 64, max_side: int = 800):
+    """`n` jobs drawn from the tiny-type and object-type scenes: kind, cascade depth 1..4,
+    image width and height uniform in [min_side, max_side], a camera on the radius-4 upper
+    hemisphere.  Returns (scenes, jobs): scenes[(kind, levels)] = Scene, and per job a dict
+    with scene key, width, height and rays."""
+    rng = np.random.default_rng(seed)
+    scenes_out = {}
+    jobs = []
+    for j in range(n):
+        kind = "tiny" if rng.random() < 0.5 else "object"
+        levels = int(rng.integers(1, 5))
+        W = int(rng.integers(min_side, max_side + 1))
+        H = int(rng.integers(min_side, max_side + 1))
+        key = (kind, levels)
+        if key not in scenes_out:
+            base = tiny_scene() if kind == "tiny" else object_scene()
+            occ, aabbs = cascade_from(base.occ[0], levels, np.random.default_rng(seed * 10 + levels))
+            scenes_out[key] = Scene(occ=occ, aabbs=aabbs, params=base.params, field=base.field,
+                                    name=f"{kind}-L{levels}")
+        cam = orbit_camera(rng, 4.0, W, H, 0.69)
+        o, d = cam.rays()
+        jobs.append({"scene": key, "width": W, "height": H, "rays_o": o, "rays_d": d})
+    return scenes_out, jobs
