@@ -134,7 +134,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2404_10272_gb300 import hdda, scenes
+    from paper_2404_10272_gb300 import hdda, replicas, scenes
 
     sc = scenes.object_scene()
     cams = scenes.object_cameras(n=N_CAMERAS)
@@ -162,7 +162,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def cam_of(j):
-        return (rank * 7 + j) % N_CAMERAS
+        return replicas.camera_for(rank, j, N_CAMERAS)
 
     def step_hdda(j):
         c = cam_of(j)
@@ -221,11 +221,7 @@ def run_ours(args):
             hdda.profiler_enable(False)
             kern = hdda.profiler_read()
         clk = clocks.stop() if clocks else None
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), device="cuda")
         return ms, samples, kern, clk
 
     K, W = args.steps, args.warmup
@@ -236,8 +232,7 @@ def run_ours(args):
     ms_sd, samp_sd, _, _ = timed(sampler_dense, max(3, K // 2), 2)
     ms_sp, samp_sp, _, _ = timed(sampler_hdda_plain, max(3, K // 2), 2)
 
-    total_rays = n * K * world
-    value = total_rays / (ms / 1e3)
+    value = replicas.aggregate_rate(n * K, ms, world)
 
     # --- end to end through the public API with host buffers ---------------
     e2e = None

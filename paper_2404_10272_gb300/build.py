@@ -59,10 +59,23 @@ def is_stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles every CUDA source for sm_103a and links libhdda.so."""
+    """Compiles every CUDA source for sm_103a and links libhdda.so.  Concurrent
+    callers (one per rank) serialise on a lock file; the first one builds."""
     if not force and not is_stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    import fcntl
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not is_stale():
+                return LIB
+            return _build_locked(verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool) -> str:
     extra = ["-Xptxas", "-v"] if (verbose or os.environ.get("HDDA_PTXAS_VERBOSE")) else []
 
     def compile_one(item):
