@@ -35,14 +35,16 @@ if ROOT not in sys.path:
 
 N_CAMERAS = 20
 L2_FLUSH_BYTES = 256 << 20
-# FP32-pipe instructions per blob evaluation in the compositor: 3 sub, 1 mul
-# + 2 fma (squared distance), 1 mul (exponent scale), 1 mul (amplitude),
-# 1 add (density), 3 fma (colour); the exp2 runs on the MUFU pipe alongside.
-COMPOSITE_FP32_PER_BLOB = 12
+# FP32-pipe instructions per evaluated blob in the compositor: 3 sub, 1 mul + 2 fma
+# (squared distance), 1 fma (scaled exponent plus log2 amplitude), 1 add (density),
+# 3 fma (colour); the exp2 runs on the MUFU pipe alongside.  The compositor skips
+# blobs beyond 7 s of a chunk by definition; the library counts the evaluations it
+# does make while profiling ("composite_blob_evals").
+COMPOSITE_FP32_PER_BLOB = 11
 KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # DRAM bytes (read + write) per launch from ncu --set full of the object-centric step, for the
 # roofline's "traffic"; an entry must be dropped whenever its kernel changes.
-PROFILED_TRAFFIC = {"composite": 238_345_472}
+PROFILED_TRAFFIC = {}
 
 
 def parse_args():
@@ -52,12 +54,14 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-stride", type=int, default=16,
-                    help="CPU baseline sample: every n-th ray of camera 0")
-    ap.add_argument("--workload", choices=["object", "batch", "serve"], default="object",
-                    help="object: the per-frame step (default line); batch: 64 mixed jobs in one "
-                         "graph launch against 64 separate launches; serve: continuous-batching "
-                         "render server under Poisson load")
+    ap.add_argument("--cpu-stride", type=int, default=None,
+                    help="CPU baseline sample: every n-th ray of camera 0 (default per workload)")
+    ap.add_argument("--workload", choices=["object", "unbounded", "tiny", "batch", "serve"],
+                    default="object",
+                    help="object / unbounded / tiny: the per-frame step on that scene (object is "
+                         "the default line); batch: 64 mixed jobs in one graph launch against 64 "
+                         "separate launches; serve: continuous-batching render server under "
+                         "Poisson load")
     ap.add_argument("--profile-step", choices=["hdda", "dense"], default=None,
                     help="profiling aid: one count-only call, one warm-up step and one step of "
                          "the given path on camera 0, no timing, no JSON line")
@@ -120,6 +124,33 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def frame_workload(name: str):
+    """(scene, 20 cameras, description, default CPU-baseline stride) of a per-frame workload."""
+    from paper_2404_10272_gb300 import scenes
+    if name == "unbounded":
+        sc = scenes.unbounded_scene()
+        cams = [scenes.unbounded_camera(j=j) for j in range(N_CAMERAS)]
+        desc = ("unbounded: 4x128^3 cascade, level l over [-2^l,2^l)^3, 1245x825 rays from "
+                "inside the inner box, 20 cameras, near 0.02, far 1e3, step 1.73e-3, cone 0.004, "
+                "64-blob composite")
+        return sc, cams, desc, 64
+    if name == "tiny":
+        sc = scenes.tiny_scene()
+        cams = [scenes.tiny_camera(seed=1001 + 7 * j) for j in range(N_CAMERAS)]
+        desc = ("tiny: 1x64^3 grid over [-1.5,1.5)^3, 96x96 rays, 20 cameras on a radius-4 "
+                "sphere, near 2, far 6, step 5e-3, 64-blob composite")
+        return sc, cams, desc, 1
+    sc = scenes.object_scene()
+    cams = scenes.object_cameras(n=N_CAMERAS)
+    desc = ("object-centric: 1x128^3 grid over [-1.5,1.5)^3, 800x800 rays, 20 cameras on a "
+            "radius-4 sphere, near 2, far 6, step 0.0050743674, 64-blob composite")
+    return sc, cams, desc, 16
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -136,8 +167,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2404_10272_gb300 import hdda, replicas, scenes
 
-    sc = scenes.object_scene()
-    cams = scenes.object_cameras(n=N_CAMERAS)
+    sc, cams, desc, stride = frame_workload(args.workload)
     rays = [c.rays() for c in cams]
     n = rays[0][0].shape[0]
     O = torch.stack([torch.from_numpy(o) for o, _ in rays]).cuda()
@@ -228,6 +258,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     ms, samples, kern, clk = timed(step_hdda, K, W, profile=True, clocks=clocks)
     ms_dense, samples_dense, kern_dense, _ = timed(step_dense, max(3, K // 2), 2, profile=True)
+    kern_dense.pop("composite_blob_evals", None)
     ms_sh, samp_sh, _, _ = timed(sampler_hdda, K, 2)
     ms_sd, samp_sd, _, _ = timed(sampler_dense, max(3, K // 2), 2)
     ms_sp, samp_sp, _, _ = timed(sampler_hdda_plain, max(3, K // 2), 2)
@@ -289,7 +320,8 @@ def run_ours(args):
         "build_vdb": sc.occ.size + grid_bytes,
         "composite": 24 * n + 8 * (n + 1) + 8 * S_avg + 16 * n + 32 * G,
     }
-    alg_inst = {"composite": S_avg * G * COMPOSITE_FP32_PER_BLOB}
+    evals = kern.pop("composite_blob_evals", (0, 0.0))[0]
+    alg_inst = {"composite": evals / K * COMPOSITE_FP32_PER_BLOB}
     per_kernel = {}
     for name, (launches, tot_ms) in kern.items():
         avg = tot_ms / max(1, launches)
@@ -299,6 +331,7 @@ def run_ours(args):
             ent["gbs"] = round(alg_bytes[name] / (avg / 1e3) / 1e9, 1)
         if name in alg_inst:
             ent["tinst_s"] = round(alg_inst[name] / (avg / 1e3) / 1e12, 2)
+            ent["blob_evals_per_sample"] = round(evals / K / max(S_avg, 1), 2)
         per_kernel[name] = ent
 
     def roof(name):
@@ -337,17 +370,15 @@ def run_ours(args):
     # --- CPU oracle on a bounded sample (rank 0, N = 1) -------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(sc, rays[0], args.cpu_stride)
+        cpu = cpu_baseline(sc, rays[0], args.cpu_stride or stride)
 
     line = {
         "metric": "rays/sec and samples/sec, HDDA vs dense-DDA on same GB300 (bit-exact); % HBM roofline",
         "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(ms / K, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "object-centric: 1x128^3 grid over [-1.5,1.5)^3, 800x800 rays, "
-                               "20 cameras on a radius-4 sphere, near 2, far 6, step 0.0050743674, "
-                               "64-blob composite",
-                   "rays_per_step": n, "occupancy": round(sc.info["occupancy"], 4),
+        "config": {"workload": desc, "rays_per_step": n,
+                   "occupancy": [round(float(sc.occ[l].mean()), 4) for l in range(sc.levels)],
                    "step": "vdb rebuild + hdda count/scan/emit + composite",
                    "l2": "flushed between steps (256 MiB write), flush outside timed windows",
                    "parallelism": f"replicas x{world}"},
@@ -419,9 +450,8 @@ def run_reference(args):
     from paper_2404_10272_gb300 import scenes
 
     oracle.build()
-    sc = scenes.object_scene()
-    cams = scenes.object_cameras(n=N_CAMERAS)
-    stride = 256  # each step: every 256th ray of one camera (2500 rays)
+    sc, cams, desc, cpu_stride = frame_workload(args.workload)
+    stride = 16 * cpu_stride  # each step: a bounded sample of one camera's rays
 
     def step(j):
         o, d = cams[j % N_CAMERAS].rays()
@@ -450,8 +480,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "object-centric: 1x128^3 grid, 800x800 rays, 20 cameras, "
-                               "64-blob composite", "parallelism": "cpu, 1 thread"},
+        "config": {"workload": desc, "parallelism": "cpu, 1 thread"},
         "cpu_baseline": {"value": round(v, 1), "unit": "rays/s", "cores": 1, "kind": "oracle",
                          "sample": f"each step: every {stride}th ray of one camera"},
         "e2e": {"value": round(v, 1), "unit": "rays/s", "h2d_bytes_per_step": 0,
@@ -465,10 +494,10 @@ def profile_step(args):
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2404_10272_gb300 import hdda, scenes
+    from paper_2404_10272_gb300 import hdda
 
-    sc = scenes.object_scene()
-    o, d = scenes.object_cameras(n=1)[0].rays()
+    sc, cams, _, _ = frame_workload(args.workload)
+    o, d = cams[0].rays()
     O, D = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
     dense = torch.from_numpy(sc.occ).cuda()
     field = torch.from_numpy(sc.field).cuda()

@@ -344,7 +344,10 @@ void hdda_batch_free(hdda_batch* batch);
  *   rays_o, rays_d  device float [n_rays][3]
  *   offsets         device int64 [n_rays + 1] (as written by a traversal)
  *   t0, t1          device float samples
- *   field           device float [n_gauss][8] = mu_x, mu_y, mu_z, s, a, r, g, b
+ *   field           device float [n_gauss][8] = mu_x, mu_y, mu_z, s, a, r, g, b,
+ *                   with s > 0 and a >= 0.  Blobs farther than 7 s from every
+ *                   sample of a 32-sample chunk are skipped for that chunk
+ *                   (weight below a * e^-24.5)
  *   n_gauss         0..256
  *   rgba_out        device float [n_rays][4]
  * Stream-ordered, no synchronisation.

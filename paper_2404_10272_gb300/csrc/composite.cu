@@ -16,12 +16,14 @@
 // exponent prescaled for exp2.
 //
 // Blob culling: before evaluating a chunk, the warp takes the bounding box
-// of its 32 sample points and drops every blob whose centre lies more than
-// kCullSigmas standard deviations from that box.  A dropped blob's weight
-// at any of those points is below a * exp(-kCullSigmas^2 / 2) = a * e^-32,
-// about 1e-14 of its amplitude, so the sums change far below the
-// compositor's 1e-5 tolerance; in the object-centric scene about 24 of 64
-// blobs survive per chunk.
+// of its 32 sample points and keeps, in a shared-memory list, only the blobs
+// whose centre lies within kCullSigmas standard deviations of that box.  A
+// dropped blob's weight at any of those points is below
+// a * exp(-kCullSigmas^2 / 2) = a * e^-24.5, about 2e-11 of its amplitude,
+// so the sums change far below the compositor's 1e-5 tolerance; in the
+// object-centric scene about 20 of 64 blobs survive per chunk.  Each blob's
+// weight is one exp2 of fma(d^2, -log2(e) / (2 s^2), log2(a)), so amplitudes
+// must be non-negative.
 #include <cmath>
 
 #include "hdda_internal.cuh"
@@ -32,8 +34,11 @@ namespace {
 constexpr int kMaxGauss = 256;
 constexpr int kWarpsPerCta = 4;
 constexpr int kRaysPerWarp = 16;
-constexpr float kCullSigmas = 8.f;
+constexpr float kCullSigmas = 7.f;
 constexpr unsigned kFull = 0xffffffffu;
+
+// Blob evaluations (sample x kept blob), counted only while profiling.
+__device__ unsigned long long g_blob_evals;
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -61,17 +66,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n,
     const int64_t* __restrict__ offsets, const float* __restrict__ t0,
     const float* __restrict__ t1, const float* __restrict__ field, int G,
-    float* __restrict__ rgba) {
+    float* __restrict__ rgba, bool count_evals) {
   __shared__ float4 gpos[kMaxGauss];  // mu_x, mu_y, mu_z, -log2(e) / (2 s^2)
-  __shared__ float4 gcol[kMaxGauss];  // a, r, g, b
+  __shared__ float4 gcol[kMaxGauss];  // log2(a), r, g, b
   __shared__ float gcut[kMaxGauss];   // (kCullSigmas * s)^2
+  __shared__ uint16_t s_list[kWarpsPerCta][kMaxGauss];  // blobs kept for the current chunk
   __shared__ float s_T[kWarpsPerCta][32];
   __shared__ float4 s_C[kWarpsPerCta][32];
   for (int i = threadIdx.x; i < G; i += blockDim.x) {
     const float* f = field + 8 * i;
     const float s = f[3];
     gpos[i] = make_float4(f[0], f[1], f[2], -1.4426950408889634f / (2.f * s * s));
-    gcol[i] = make_float4(f[4], f[5], f[6], f[7]);
+    gcol[i] = make_float4(log2f(f[4]), f[5], f[6], f[7]);
     gcut[i] = (kCullSigmas * s) * (kCullSigmas * s);
   }
   __syncthreads();
@@ -134,7 +140,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
           by1 = fmaxf(by1, __shfl_xor_sync(kFull, by1, o2));
           bz1 = fmaxf(bz1, __shfl_xor_sync(kFull, bz1, o2));
         }
-        float sigma = 0.f, sr = 0.f, sg = 0.f, sbl = 0.f;
+        uint16_t* list = s_list[wib];
+        int m = 0;
         for (int q0 = 0; q0 < G; q0 += 32) {
           bool near = false;
           if (q0 + lane < G) {
@@ -144,21 +151,27 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
             const float ez = fmaxf(0.f, fmaxf(bz0 - P.z, P.z - bz1));
             near = ex * ex + ey * ey + ez * ez <= gcut[q0 + lane];
           }
-          unsigned m = __ballot_sync(kFull, near);
-          while (m) {
-            const int q = q0 + __ffs(m) - 1;
-            m &= m - 1;
-            const float4 P = gpos[q];
-            const float ex = px - P.x, ey = py - P.y, ez = pz - P.z;
-            const float d2 = ex * ex + ey * ey + ez * ez;
-            const float4 C = gcol[q];
-            const float w = C.x * ex2_approx(d2 * P.w);
-            sigma += w;
-            sr += w * C.y;
-            sg += w * C.z;
-            sbl += w * C.w;
-          }
+          const unsigned ball = __ballot_sync(kFull, near);
+          if (near) list[m + __popc(ball & ((1u << lane) - 1u))] = (uint16_t)(q0 + lane);
+          m += __popc(ball);
         }
+        if (count_evals && lane == 0)
+          atomicAdd(&g_blob_evals, (unsigned long long)m * (unsigned long long)min(wend - base, (int64_t)32));
+        __syncwarp();
+        float sigma = 0.f, sr = 0.f, sg = 0.f, sbl = 0.f;
+        for (int i = 0; i < m; ++i) {
+          const int q = list[i];
+          const float4 P = gpos[q];
+          const float ex = px - P.x, ey = py - P.y, ez = pz - P.z;
+          const float d2 = ex * ex + ey * ey + ez * ez;
+          const float4 C = gcol[q];
+          const float w = ex2_approx(fmaf(d2, P.w, C.x));
+          sigma += w;
+          sr = fmaf(w, C.y, sr);
+          sg = fmaf(w, C.z, sg);
+          sbl = fmaf(w, C.w, sbl);
+        }
+        __syncwarp();
         if (live) {
           alpha = -expm1f(-sigma * (a1 - a0));
           if (sigma > 0.f) {
@@ -202,6 +215,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
 }
 
 }  // namespace
+
+unsigned long long composite_take_blob_evals() {
+  unsigned long long v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_blob_evals, sizeof(v)) != cudaSuccess) return 0;
+  cudaMemcpyToSymbol(g_blob_evals, &zero, sizeof(zero));
+  return v;
+}
+
 }  // namespace hdda
 
 extern "C" int hdda_composite(const float* rays_o, const float* rays_d, int64_t n_rays,
@@ -224,7 +245,7 @@ extern "C" int hdda_composite(const float* rays_o, const float* rays_d, int64_t 
   const unsigned grid = (unsigned)blocks;
   KernelTimer kt("composite", (cudaStream_t)stream);
   composite_kernel<<<grid, kWarpsPerCta * 32, 0, (cudaStream_t)stream>>>(
-      rays_o, rays_d, n_rays, offsets, t0, t1, field, n_gauss, rgba_out);
+      rays_o, rays_d, n_rays, offsets, t0, t1, field, n_gauss, rgba_out, profiler_on());
   kt.stop();
   HDDA_CUDA_TRY(cudaGetLastError());
   return HDDA_OK;

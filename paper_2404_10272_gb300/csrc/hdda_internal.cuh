@@ -114,6 +114,11 @@ int set_error(int code, const char* fmt, ...);
 int cuda_error(cudaError_t e, const char* what);
 void clear_error();
 
+// True while the kernel profiler is enabled (runtime.cu).
+bool profiler_on();
+// Blob evaluations counted by the compositor since the last call (composite.cu).
+unsigned long long composite_take_blob_evals();
+
 // Brackets one kernel launch with events when the profiler is enabled.
 class KernelTimer {
  public:

@@ -52,6 +52,11 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+bool profiler_on() {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  return g_prof_on;
+}
+
 KernelTimer::KernelTimer(const char* name, cudaStream_t s, bool allow) : name_(name), s_(s) {
   if (!allow) return;
   std::lock_guard<std::mutex> lock(g_prof_mu);
@@ -111,6 +116,13 @@ extern "C" int hdda_profiler_read(hdda_kernel_time* out, int cap, int* n_out) {
     g_prof_pool.push_back(r.b);
   }
   g_prof_records.clear();
+  // work counters reported as pseudo-kernels (launches = count, no time)
+  const unsigned long long evals = composite_take_blob_evals();
+  if (evals) {
+    names.emplace_back("composite_blob_evals");
+    launches.push_back((int64_t)evals);
+    ms.push_back(0.0);
+  }
   if (n_out) *n_out = (int)names.size();
   for (int i = 0; i < (int)names.size() && i < cap && out; ++i) {
     std::memset(&out[i], 0, sizeof(out[i]));
