@@ -180,6 +180,10 @@ def run_ours(args):
     gd = hdda.pack_dense(dense, sc.aabbs)
     gvp = hdda.build_vdb(dense, sc.aabbs)   # the plain VDB tree, without refinement masks
     gvp.set_refine(False)
+    gvs = hdda.build_vdb(dense, sc.aabbs)   # Algorithm 2's control flow ("skip")
+    gvs.set_walk(hdda.WALK_SKIP)
+    gds = hdda.pack_dense(dense, sc.aabbs)
+    gds.set_walk(hdda.WALK_SKIP)
     vstats = gv.stats()
     plain_bytes = int(gvp.stats().bytes)
 
@@ -215,6 +219,14 @@ def run_ours(args):
     def sampler_hdda_plain(j):
         c = cam_of(j)
         return hdda.traverse_hdda(O[c], D[c], gvp, prm, out=bufs).total
+
+    def sampler_hdda_skip(j):
+        c = cam_of(j)
+        return hdda.traverse_hdda(O[c], D[c], gvs, prm, out=bufs).total
+
+    def sampler_dense_skip(j):
+        c = cam_of(j)
+        return hdda.traverse_dense(O[c], D[c], gds, prm, out=bufs).total
 
     def sampler_dense(j):
         c = cam_of(j)
@@ -262,6 +274,8 @@ def run_ours(args):
     ms_sh, samp_sh, _, _ = timed(sampler_hdda, K, 2)
     ms_sd, samp_sd, _, _ = timed(sampler_dense, max(3, K // 2), 2)
     ms_sp, samp_sp, _, _ = timed(sampler_hdda_plain, max(3, K // 2), 2)
+    ms_ss, _, _, _ = timed(sampler_hdda_skip, max(3, K // 2), 2)
+    ms_ds, _, _, _ = timed(sampler_dense_skip, max(3, K // 2), 2)
 
     value = replicas.aggregate_rate(n * K, ms, world)
 
@@ -394,6 +408,10 @@ def run_ours(args):
                                    "ms_per_frame": round(ms_sp / max(3, K // 2), 4),
                                    "note": "HDDA on the plain VDB tree (8^3 leaves, 16^3-block "
                                            "nodes), refinement masks off"},
+        "skip_form_samplers": {
+            "note": "Algorithm 2 control flow (leading empty regions in an inner loop); same samples",
+            "hdda_ms_per_frame": round(ms_ss / max(3, K // 2), 4),
+            "dense_ms_per_frame": round(ms_ds / max(3, K // 2), 4)},
         "dense_dda_step": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_dense / 1e3), 1),
                            "ms_per_step": round(ms_dense / max(3, K // 2), 4)},
         "hdda_vs_dense_sampler_speedup": round(ms_sd / max(3, K // 2) / (ms_sh / K), 3),

@@ -207,6 +207,20 @@ int hdda_grid_copy_array(const hdda_grid* grid, int which, void* dst, size_t byt
  */
 int hdda_grid_set_refine(hdda_grid* grid, int on);
 
+/*
+ * Control flow of the per-ray walk of hdda_traverse_dense / hdda_traverse_hdda
+ * on this grid (supplementary material, Algorithms 1 and 2):
+ *   HDDA_WALK_BRANCH (default): one region per step, branching on its
+ *     occupancy ("DDA branch", Algorithm 1);
+ *   HDDA_WALK_SKIP: every run of leading empty regions is crossed in an
+ *     inner loop before the occupied region is taken ("DDA skip",
+ *     Algorithm 2, read as t1 <- t_last and `until grid.at(ijk)`).
+ * The samples are identical; only the SIMT schedule differs.  Batches and
+ * hdda_traverse_hdda_noalloc always use the branch form.
+ */
+typedef enum { HDDA_WALK_BRANCH = 0, HDDA_WALK_SKIP = 1 } hdda_walk_variant;
+int hdda_grid_set_walk(hdda_grid* grid, int variant);
+
 /* Frees a grid (waits for the device to finish with it).  NULL is a no-op. */
 void hdda_grid_free(hdda_grid* grid);
 

@@ -520,6 +520,15 @@ extern "C" int hdda_grid_set_refine(hdda_grid* g, int on) {
   return HDDA_OK;
 }
 
+extern "C" int hdda_grid_set_walk(hdda_grid* g, int variant) {
+  clear_error();
+  if (!g) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
+  if (variant != HDDA_WALK_BRANCH && variant != HDDA_WALK_SKIP)
+    return set_error(HDDA_ERR_INVALID_ARG, "walk variant %d unknown", variant);
+  g->walk_variant = variant;
+  return HDDA_OK;
+}
+
 extern "C" void hdda_grid_free(hdda_grid* g) {
   if (!g) return;
   if (g->built) {

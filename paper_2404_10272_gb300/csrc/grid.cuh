@@ -24,6 +24,7 @@ struct hdda_grid {
   uint32_t* nsuper = nullptr;    // vdb [L*N^3][kSuperWords] refinement masks
   uint32_t* lsub = nullptr;      // vdb [L*B^3][kLeafSubWords] capacity, per leaf
   int refine = 1;                // HDDA uses the refinement masks
+  int walk_variant = HDDA_WALK_BRANCH;  // control flow of the two-pass walk
   // build temporaries (kept so that a rebuild allocates nothing)
   uint32_t* blk_masks = nullptr; // [L*B^3][16]
   uint8_t* blk_state = nullptr;  // [L*B^3]

@@ -291,7 +291,7 @@ __device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, in
 // Pass 1.  Persistent: each warp takes 32-ray tiles in order until none is
 // left, so a warp never waits for another.  Writes counts[r], nruns[r]
 // (saturated at 255) and the first kMaxRuns runs at runs[r + j * n].
-template <int kMode, bool kSm>
+template <int kMode, bool kSm, bool kSkip>
 __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, int32_t* __restrict__ counts, uint8_t* __restrict__ nruns_out,
@@ -347,8 +347,8 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
       Ray ray;
       int nr = 0;
       if (load_ray(ro, rd, r, ray))
-        c = walk<kMode, false, kSm>(g, tb, ls, h, ray, runs + r, n, nr, 0, 0, 0, nullptr, nullptr,
-                                   nullptr, status);
+        c = walk<kMode, false, kSm, kSkip>(g, tb, ls, h, ray, runs + r, n, nr, 0, 0, 0, nullptr,
+                                          nullptr, nullptr, status);
       counts[r] = (int32_t)c;
       nruns_out[r] = (uint8_t)min(nr, 255);
     }
@@ -601,9 +601,9 @@ struct WalkArgs {
   unsigned* status;
 };
 
-template <int kMode, bool kSm>
+template <int kMode, bool kSm, bool kSkip>
 int launch_walk(const WalkArgs& w, size_t smem, cudaStream_t s) {
-  auto kern = walk_kernel<kMode, kSm>;
+  auto kern = walk_kernel<kMode, kSm, kSkip>;
   if (smem > 48 * 1024)
     HDDA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
@@ -621,9 +621,12 @@ int launch_walk(const WalkArgs& w, size_t smem, cudaStream_t s) {
 }
 
 template <int kMode>
-int launch_walk_mode(const WalkArgs& w, size_t stage_bytes, cudaStream_t s) {
-  return stage_bytes <= kMaxStageBytes ? launch_walk<kMode, true>(w, stage_bytes, s)
-                                       : launch_walk<kMode, false>(w, 0, s);
+int launch_walk_mode(const WalkArgs& w, size_t stage_bytes, bool skip, cudaStream_t s) {
+  if (skip)
+    return stage_bytes <= kMaxStageBytes ? launch_walk<kMode, true, true>(w, stage_bytes, s)
+                                         : launch_walk<kMode, false, true>(w, 0, s);
+  return stage_bytes <= kMaxStageBytes ? launch_walk<kMode, true, false>(w, stage_bytes, s)
+                                       : launch_walk<kMode, false, false>(w, 0, s);
 }
 
 const char* walk_name(int mode) {
@@ -661,9 +664,10 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   const size_t stage = stage_layout(lat.K, w.g.L, w.g.R, grid->nodes_total(), mode).bytes;
   {
     KernelTimer kt(walk_name(mode), s);
-    const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, s)
-                   : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, s)
-                                      : launch_walk_mode<kModeVdbRefined>(w, stage, s);
+    const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
+    const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, skip, s)
+                   : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, skip, s)
+                                      : launch_walk_mode<kModeVdbRefined>(w, stage, skip, s);
     if (st != HDDA_OK) return st;
   }
   {

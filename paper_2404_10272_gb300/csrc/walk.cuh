@@ -327,7 +327,11 @@ __device__ __forceinline__ int cross(const Ray& r, const LatticeDev& lat, const 
 // [k_begin, k_end): the first kMaxRuns go to runs[j * stride]; nruns counts
 // all.  With kEmit it instead writes the samples from `out`, below
 // `capacity` (lat.t must then be a global-memory table).
-template <int kMode, bool kEmit, bool kSm>
+// kSkip selects the control flow of Algorithm 2 ("DDA skip": cross every
+// leading empty region in an inner loop, then take the occupied one)
+// instead of Algorithm 1 ("DDA branch": one region per iteration, branching
+// on its occupancy).  The regions crossed, and so the samples, are the same.
+template <int kMode, bool kEmit, bool kSm, bool kSkip = false>
 __device__ __forceinline__ int64_t walk(const GridDev& g, const Tabs& tb, const LatticeDev& lat,
                                         const LatHdr& h, const Ray& r, uint2* runs,
                                         int64_t stride, int& nruns, int32_t rid,
@@ -344,9 +348,17 @@ __device__ __forceinline__ int64_t walk(const GridDev& g, const Tabs& tb, const 
   int k = 0;
   while (k < K) {
     float e[3];
-    const bool occ = locate<kMode, kSm>(g, tb, r, x, e);
+    bool occ = locate<kMode, kSm>(g, tb, r, x, e);
     if (outside(x, e, r)) atomicOr(status, kDevInternal);  // region must hold its point
-    const int kn = cross<kSm>(r, lat, h, k, e, x);
+    int kn = cross<kSm>(r, lat, h, k, e, x);
+    if constexpr (kSkip) {
+      while (!occ && kn < K) {  // leading empty regions
+        k = kn;
+        occ = locate<kMode, kSm>(g, tb, r, x, e);
+        if (outside(x, e, r)) atomicOr(status, kDevInternal);
+        kn = cross<kSm>(r, lat, h, k, e, x);
+      }
+    }
     if (occ) {
       if (kEmit) {
         float ta = __ldg(lat.t + k);

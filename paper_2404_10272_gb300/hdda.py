@@ -20,6 +20,7 @@ from . import build as _build
 OK = 0
 ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_STEP_LIMIT, ERR_TIMEOUT, ERR_OOM, ERR_INTERNAL = range(1, 8)
 GRID_DENSE, GRID_VDB = 0, 1
+WALK_BRANCH, WALK_SKIP = 0, 1
 (ARRAY_THRESHOLDS, ARRAY_DENSE_BITS, ARRAY_CHILD_MASK, ARRAY_TILE_MASK, ARRAY_LEAF_PREFIX,
  ARRAY_LEAVES, ARRAY_NODE_SUPER, ARRAY_LEAF_SUB) = range(8)
 
@@ -28,7 +29,7 @@ EXPORTED = [
     "hdda_grid_stats_get", "hdda_grid_copy_array", "hdda_grid_free", "hdda_traverse_dense",
     "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
     "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine", "hdda_batch_create",
-    "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free",
+    "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free", "hdda_grid_set_walk",
 ]
 
 
@@ -99,6 +100,7 @@ def load(path: str | None = None):
     lib.hdda_grid_stats_get.argtypes = [vp, ctypes.POINTER(GridStats)]
     lib.hdda_grid_copy_array.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hdda_grid_set_refine.argtypes = [vp, i32]
+    lib.hdda_grid_set_walk.argtypes = [vp, i32]
     lib.hdda_batch_create.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(BatchConfig),
                                       ctypes.POINTER(vp), vp]
     lib.hdda_batch_launch.argtypes = [vp, vp]
@@ -189,6 +191,10 @@ class Grid:
     def set_refine(self, on: bool):
         """VDB grids: walk with (True, default) or without the refinement masks."""
         _check(load().hdda_grid_set_refine(self._h, 1 if on else 0))
+
+    def set_walk(self, variant: int):
+        """WALK_BRANCH (Algorithm 1, default) or WALK_SKIP (Algorithm 2) control flow."""
+        _check(load().hdda_grid_set_walk(self._h, int(variant)))
 
     def rebuild(self, dense: torch.Tensor, stream=None):
         d = _cuda(dense, torch.uint8)

@@ -47,6 +47,12 @@ def check_all(H, occ, aabbs, o, d, p, what):
     gv.set_refine(False)
     plain = gpu_samples(H, "hdda", ot, dt, gv, prm)
     assert_same(plain, ref, what + " HDDA without refinement vs oracle")
+    gv.set_refine(True)
+    # Algorithm 2's control flow gives the same samples as Algorithm 1's
+    for g, kind in ((gv, "hdda"), (gd, "dense")):
+        g.set_walk(H.WALK_SKIP)
+        assert_same(gpu_samples(H, kind, ot, dt, g, prm), ref, what + f" {kind} skip form")
+        g.set_walk(H.WALK_BRANCH)
     return ref
 
 
