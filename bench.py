@@ -93,7 +93,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -266,9 +266,20 @@ def run_ours(args):
         ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), device="cuda")
         return ms, samples, kern, clk
 
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def render_step(j):
+        c = cam_of(j)
+        gv.rebuild(dense)
+        hdda.render(O[c], D[c], gv, prm, field, out=rgba, status=status)
+        return 0
+
     K, W = args.steps, args.warmup
+    # clocks are sampled over every timed loop below (the headline loop alone is
+    # shorter than a few sampling periods)
     clocks = ClockSampler(local)
-    ms, samples, kern, clk = timed(step_hdda, K, W, profile=True, clocks=clocks)
+    clocks.start()
+    ms, samples, kern, _ = timed(step_hdda, K, W, profile=True)
     ms_dense, samples_dense, kern_dense, _ = timed(step_dense, max(3, K // 2), 2, profile=True)
     kern_dense.pop("composite_blob_evals", None)
     ms_sh, samp_sh, _, _ = timed(sampler_hdda, K, 2)
@@ -276,6 +287,11 @@ def run_ours(args):
     ms_sp, samp_sp, _, _ = timed(sampler_hdda_plain, max(3, K // 2), 2)
     ms_ss, _, _, _ = timed(sampler_hdda_skip, max(3, K // 2), 2)
     ms_ds, _, _, _ = timed(sampler_dense_skip, max(3, K // 2), 2)
+    ms_r, _, kern_r, _ = timed(render_step, K, 2, profile=True)
+    clk = clocks.stop()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"hdda_render raised device status {int(status.item())}")
+    render_evals = kern_r.pop("render_blob_evals", (0, 0.0))[0]
 
     value = replicas.aggregate_rate(n * K, ms, world)
 
@@ -414,6 +430,17 @@ def run_ours(args):
             "dense_ms_per_frame": round(ms_ds / max(3, K // 2), 4)},
         "dense_dda_step": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_dense / 1e3), 1),
                            "ms_per_step": round(ms_dense / max(3, K // 2), 4)},
+        "render_only_step": {
+            "note": "vdb rebuild + hdda_render: the walk, then runs expanded from the lattice "
+                    "table and composited in one kernel; no sample, scan or host read-back",
+            "rays_per_s": round(n * K * world / (ms_r / 1e3), 1),
+            "ms_per_step": round(ms_r / K, 4),
+            "vs_step": round(ms / ms_r, 3),
+            "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}
+                        for k, v in kern_r.items()},
+            "render_tinst_s": (round(render_evals / K * COMPOSITE_FP32_PER_BLOB
+                                     / (kern_r["hdda_render"][1] / kern_r["hdda_render"][0] / 1e3)
+                                     / 1e12, 2) if "hdda_render" in kern_r else None)},
         "hdda_vs_dense_sampler_speedup": round(ms_sd / max(3, K // 2) / (ms_sh / K), 3),
         "grid": {"vdb_bytes": grid_bytes, "vdb_plain_bytes": plain_bytes,
                  "dense_bytes": int(vstats.dense_bytes),

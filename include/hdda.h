@@ -371,6 +371,30 @@ int hdda_composite(const float* rays_o, const float* rays_d, int64_t n_rays,
                    const float* field, int n_gauss, float* rgba_out, hdda_stream_t stream);
 
 /*
+ * Render-only path: samples and composites in one call without writing any
+ * sample to memory (the sampler and the field evaluation fused).  Ray r's
+ * pixel is the one hdda_composite gives for the intervals that
+ * hdda_traverse_hdda (VDB grid) or hdda_traverse_dense (dense grid) keeps
+ * for it, up to float summation order (both are within 1e-5 of the same
+ * FP64 accumulation).  A VDB grid is walked by HDDA with its refinement and
+ * walk-variant settings, a dense grid by dense DDA.
+ *   rays_o, rays_d, n_rays, grid, params   as for hdda_traverse_hdda
+ *   field, n_gauss, rgba_out               as for hdda_composite
+ *   dev_status   NULL: the call synchronises the stream once at the end and
+ *                returns HDDA_ERR_INTERNAL if a device-side region check
+ *                failed.  Otherwise a DEVICE uint32 (4-byte aligned) that
+ *                receives the device status bits by atomic OR (bit 1 =
+ *                region check failed); the call then returns once the work
+ *                is enqueued and does not synchronise, except on the first
+ *                use of a parameter set (the lattice is computed then).
+ * Scratch of about 134 bytes per ray comes from the stream-ordered allocator
+ * and is returned in stream order.
+ */
+int hdda_render(const float* rays_o, const float* rays_d, int64_t n_rays,
+                const hdda_grid* grid, const hdda_params* params, const float* field,
+                int n_gauss, float* rgba_out, uint32_t* dev_status, hdda_stream_t stream);
+
+/*
  * Kernel timing for measurement.  While enabled, every kernel the library
  * launches is bracketed by two CUDA events recorded on the stream it is
  * launched on.  hdda_profiler_read synchronises on those events, writes up

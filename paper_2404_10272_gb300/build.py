@@ -29,6 +29,7 @@ SOURCES = {
     "composite.cu": [],
     "noalloc.cu": [],
     "batch.cu": ["-fmad=false"],
+    "render.cu": ["-fmad=false"],
 }
 
 

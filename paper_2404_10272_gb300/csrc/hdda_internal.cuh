@@ -118,6 +118,8 @@ void clear_error();
 bool profiler_on();
 // Blob evaluations counted by the compositor since the last call (composite.cu).
 unsigned long long composite_take_blob_evals();
+// The same count for the render-only path (render.cu).
+unsigned long long render_take_blob_evals();
 
 // Brackets one kernel launch with events when the profiler is enabled.
 class KernelTimer {

@@ -1,0 +1,272 @@
+// render.cu -- the render-only path: the sampler and the compositor joined
+// at the level of runs, so that no sample is ever written to memory (the
+// fused sampler + field evaluation; Sec. 1's accumulation applied to the
+// intervals Algorithm 1 keeps).
+//
+// Pass 1 is the samplers' walk (walk_kernel, walk.cuh): each ray's merged
+// occupied runs of lattice indices [k_begin, k_end), the first kMaxRuns of
+// them, and its number of runs.  Pass 2 (render_kernel) gives each warp 16
+// consecutive rays, as the compositor over stored samples does.  Every
+// lattice index k of a run is the sample (t_k, t_{k+1}) with midpoint tm_k,
+// read from the lattice table all rays share, so a warp numbers its rays'
+// samples locally (a warp scan of the run lengths), and lane j of each
+// 32-sample chunk finds its ray (binary search over the lanes' first
+// positions) and its run (binary search over that ray's runs in shared
+// memory).  No global scan, no sample arrays, no host read-back.
+//
+// A ray with more than kMaxRuns runs is finished in rounds: after the runs
+// it has are composited, it walks again from the end of the last one
+// (walk_from) and the next kMaxRuns runs are composited with its
+// transmittance and colour carried over, so samples are still accumulated
+// front to back.
+#include "field.cuh"
+#include "walk.cuh"
+
+namespace hdda {
+namespace {
+
+constexpr int kRenderWarps = 4;
+constexpr int kRenderRays = 16;  // rays per warp task
+constexpr uint32_t kNoRun = 0x7fffffffu;
+
+// Blob evaluations (sample x kept blob), counted only while profiling.
+__device__ unsigned long long g_render_evals;
+
+template <int kMode>
+__global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
+    const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
+    LatticeDev lat, const uint8_t* __restrict__ nruns, const uint2* __restrict__ runs,
+    const float* __restrict__ field, int G, float* __restrict__ rgba,
+    unsigned* __restrict__ status, bool count_evals) {
+  __shared__ BlobTables bt;
+  __shared__ uint16_t s_list[kRenderWarps][kMaxGauss];
+  __shared__ float s_T[kRenderWarps][32];
+  __shared__ float4 s_C[kRenderWarps][32];
+  // run j of ray slot i at [j * kRenderRays + i]: {first k, first position}
+  __shared__ uint2 s_run[kRenderWarps][kMaxRuns * kRenderRays];
+  stage_blobs(bt, field, G);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t task = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (task * kRenderRays >= n) return;  // uniform per warp; no block barrier follows
+  float* T_s = s_T[wib];
+  float4* C_s = s_C[wib];
+  uint2* sr = s_run[wib];
+  unsigned long long* evals = count_evals ? &g_render_evals : nullptr;
+  const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+  const int64_t r = task * kRenderRays + lane;
+  const bool has_ray = lane < kRenderRays && r < n;
+  Ray ray{};
+  const bool ok = has_ray && load_ray(ro, rd, r, ray);
+  T_s[lane] = 1.f;
+  C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int nr_all = ok ? (int)nruns[r] : 0;  // saturated at 255
+  int nr = min(nr_all, kMaxRuns);
+  for (int j = 0; j < nr; ++j) sr[j * kRenderRays + lane] = __ldg(runs + (int64_t)j * n + r);
+  int k_next = lat.K;  // where the ray's walk resumes
+  if (nr_all > kMaxRuns) k_next = (int)sr[(kMaxRuns - 1) * kRenderRays + lane].y;
+  for (;;) {
+    // this round's runs: lengths, the warp's numbering, then first positions
+    int cnt = 0;
+    for (int j = 0; j < nr; ++j) {
+      const uint2 v = sr[j * kRenderRays + lane];
+      cnt += (int)(v.y - v.x);
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const int pos = inc - cnt;
+    const int W = __shfl_sync(kFull, inc, 31);
+    if (lane < kRenderRays) {
+      int q = pos;
+      for (int j = 0; j < kMaxRuns; ++j) {
+        uint2& e = sr[j * kRenderRays + lane];
+        if (j < nr) {
+          const int len = (int)(e.y - e.x);
+          e.y = (uint32_t)q;
+          q += len;
+        } else {
+          e = make_uint2(0u, kNoRun);
+        }
+      }
+    }
+    __syncwarp();
+    for (int base = 0; base < W; base += 32) {
+      const int p = base + lane;
+      const bool live = p < W;
+      int own = 0;  // the last ray slot whose first position is <= p
+#pragma unroll
+      for (int s = kRenderRays / 2; s > 0; s >>= 1) {
+        const int v = __shfl_sync(kFull, pos, own + s);
+        if (v <= p) own += s;
+      }
+      int j = 0;  // the last run of that ray starting at or before p
+#pragma unroll
+      for (int s = kMaxRuns / 2; s > 0; s >>= 1)
+        if (sr[(j + s) * kRenderRays + own].y <= (uint32_t)p) j += s;
+      const uint2 e = sr[j * kRenderRays + own];
+      const float ox = __shfl_sync(kFull, ray.o[0], own), oy = __shfl_sync(kFull, ray.o[1], own),
+                  oz = __shfl_sync(kFull, ray.o[2], own);
+      const float dx = __shfl_sync(kFull, ray.d[0], own), dy = __shfl_sync(kFull, ray.d[1], own),
+                  dz = __shfl_sync(kFull, ray.d[2], own);
+      float a0 = 0.f, a1 = 0.f, px = 0.f, py = 0.f, pz = 0.f;
+      if (live) {
+        const int k = (int)e.x + (p - (int)e.y);
+        a0 = __ldg(lat.t + k);
+        a1 = __ldg(lat.t + k + 1);
+        const float tm = __ldg(lat.tm + k);
+        px = fmaf(tm, dx, ox);
+        py = fmaf(tm, dy, oy);
+        pz = fmaf(tm, dz, oz);
+      }
+      composite_chunk(bt, G, s_list[wib], live, p + 1 >= W, own, px, py, pz, a0, a1, T_s, C_s,
+                      evals);
+    }
+    const bool more = k_next < lat.K;
+    if (!__any_sync(kFull, more)) break;
+    nr = 0;
+    if (more)
+      k_next = walk_from<kMode, false>(g, global_tabs(g), lat, h, ray, k_next, sr + lane,
+                                       kRenderRays, nr, status);
+    __syncwarp();
+  }
+  if (has_ray) {
+    const float4 acc = C_s[lane];
+    reinterpret_cast<float4*>(rgba)[r] = make_float4(acc.x, acc.y, acc.z, 1.f - T_s[lane]);
+  }
+}
+
+const char* render_name(int mode) {
+  return mode == kModeDense ? "dense_render" : mode == kModeVdb ? "hdda_render_plain"
+                                                                 : "hdda_render";
+}
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch: [0, 256) header {walk counter u32, status u32}, then tile sums,
+// counts, run counts and runs.
+size_t render_scratch_bytes(int64_t n) {
+  const int64_t T = (n + 31) / 32;
+  return 256 + a256(8 * (size_t)T) + a256(4 * (size_t)n) + a256((size_t)n) +
+         a256(sizeof(uint2) * kMaxRuns * (size_t)n);
+}
+
+// Pinned host word for the synchronous status read.
+struct HostWord {
+  unsigned* p = nullptr;
+  ~HostWord() { if (p) cudaFreeHost(p); }
+};
+thread_local HostWord t_word;
+
+int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+                  const LatticeDev& lat, const float* field, int G, float* rgba,
+                  unsigned* dev_status, char* scratch, cudaStream_t s) {
+  const int64_t T = (n + 31) / 32;
+  unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+  unsigned* status = dev_status ? dev_status : counter + 1;
+  char* p = scratch + 256;
+  int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
+  p += a256(8 * (size_t)T);
+  int32_t* counts = reinterpret_cast<int32_t*>(p);
+  p += a256(4 * (size_t)n);
+  uint8_t* nr = reinterpret_cast<uint8_t*>(p);
+  p += a256((size_t)n);
+  uint2* runs = reinterpret_cast<uint2*>(p);
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+  const int mode = walk_mode(grid);
+  const WalkArgs w{ro, rd, n, grid->view(), lat, counts, nr, runs, tile_sum, counter, status};
+  const size_t stage = stage_layout(lat.K, w.g.L, w.g.R, grid->nodes_total(), mode).bytes;
+  {
+    KernelTimer kt(walk_name(mode), s);
+    const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
+    const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, skip, s)
+                   : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, skip, s)
+                                      : launch_walk_mode<kModeVdbRefined>(w, stage, skip, s);
+    if (st != HDDA_OK) return st;
+  }
+  {
+    KernelTimer kt(render_name(mode), s);
+    const int64_t warps = (n + kRenderRays - 1) / kRenderRays;
+    const unsigned nb = (unsigned)((warps + kRenderWarps - 1) / kRenderWarps);
+    const bool ev = profiler_on();
+    switch (mode) {
+      case kModeDense:
+        render_kernel<kModeDense><<<nb, kRenderWarps * 32, 0, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
+        break;
+      case kModeVdb:
+        render_kernel<kModeVdb><<<nb, kRenderWarps * 32, 0, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
+        break;
+      default:
+        render_kernel<kModeVdbRefined><<<nb, kRenderWarps * 32, 0, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
+        break;
+    }
+  }
+  HDDA_CUDA_TRY(cudaGetLastError());
+  return HDDA_OK;
+}
+
+}  // namespace
+
+unsigned long long render_take_blob_evals() {
+  unsigned long long v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_render_evals, sizeof(v)) != cudaSuccess) return 0;
+  cudaMemcpyToSymbol(g_render_evals, &zero, sizeof(zero));
+  return v;
+}
+
+}  // namespace hdda
+
+extern "C" int hdda_render(const float* rays_o, const float* rays_d, int64_t n_rays,
+                           const hdda_grid* grid, const hdda_params* params, const float* field,
+                           int n_gauss, float* rgba_out, uint32_t* dev_status,
+                           hdda_stream_t stream) {
+  using namespace hdda;
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!grid) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
+  if (n_rays < 0 || n_rays > INT32_MAX)
+    return set_error(HDDA_ERR_INVALID_ARG, "n_rays=%lld", (long long)n_rays);
+  if (n_gauss < 0 || n_gauss > kMaxGauss)
+    return set_error(HDDA_ERR_INVALID_ARG, "n_gauss=%d outside 0..%d", n_gauss, kMaxGauss);
+  if (n_rays > 0 && (!rays_o || !rays_d || !rgba_out))
+    return set_error(HDDA_ERR_INVALID_ARG, "NULL pointer");
+  if (n_gauss > 0 && !field) return set_error(HDDA_ERR_INVALID_ARG, "field is NULL");
+  if (reinterpret_cast<uintptr_t>(rgba_out) % 16 != 0)
+    return set_error(HDDA_ERR_INVALID_ARG, "rgba_out must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(dev_status) % 4 != 0)
+    return set_error(HDDA_ERR_INVALID_ARG, "dev_status must be 4-byte aligned");
+  int dev = 0;
+  HDDA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != grid->device)
+    return set_error(HDDA_ERR_INVALID_ARG, "grid lives on device %d, current is %d",
+                     grid->device, dev);
+  LatticeDev lat;
+  int st = lattice_for(params, s, &lat);
+  if (st != HDDA_OK) return st;
+  if (n_rays == 0) return HDDA_OK;
+  unsigned* hw = nullptr;
+  if (!dev_status) {
+    if (!t_word.p) HDDA_CUDA_TRY(cudaMallocHost(&t_word.p, sizeof(unsigned)));
+    hw = t_word.p;
+  }
+  char* scratch = nullptr;
+  HDDA_CUDA_TRY(cudaMallocAsync(&scratch, render_scratch_bytes(n_rays), s));
+  st = launch_render(rays_o, rays_d, n_rays, grid, lat, field, n_gauss, rgba_out, dev_status,
+                     scratch, s);
+  if (st == HDDA_OK && !dev_status) {
+    cudaError_t e = cudaMemcpyAsync(hw, scratch + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_error(e, "cudaMemcpyAsync(status)");
+  }
+  cudaError_t e = cudaFreeAsync(scratch, s);
+  if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
+  if (st != HDDA_OK || dev_status) return st;
+  HDDA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (*hw & kDevInternal) return set_error(HDDA_ERR_INTERNAL, "region check failed on the device");
+  return HDDA_OK;
+}

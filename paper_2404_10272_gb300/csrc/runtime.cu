@@ -117,10 +117,12 @@ extern "C" int hdda_profiler_read(hdda_kernel_time* out, int cap, int* n_out) {
   }
   g_prof_records.clear();
   // work counters reported as pseudo-kernels (launches = count, no time)
-  const unsigned long long evals = composite_take_blob_evals();
-  if (evals) {
-    names.emplace_back("composite_blob_evals");
-    launches.push_back((int64_t)evals);
+  const unsigned long long evals[2] = {composite_take_blob_evals(), render_take_blob_evals()};
+  const char* const eval_names[2] = {"composite_blob_evals", "render_blob_evals"};
+  for (int i = 0; i < 2; ++i) {
+    if (!evals[i]) continue;
+    names.emplace_back(eval_names[i]);
+    launches.push_back((int64_t)evals[i]);
     ms.push_back(0.0);
   }
   if (n_out) *n_out = (int)names.size();

@@ -254,110 +254,6 @@ __global__ void __launch_bounds__(kBS) onepass_kernel(
 // two-pass sampler: walk (persistent warps, staged tables), then emit
 // ---------------------------------------------------------------------------
 
-constexpr int kWalkBS = 256;
-
-// Shared-memory bytes that stage the walk's tables (0 = they do not fit).
-struct StageLayout {
-  size_t tm, kidx, thr, child, tile, prefix, nstate, nsuper, bytes;
-};
-
-__host__ __device__ inline StageLayout stage_layout(int K, int L, int R, int64_t nodes, int mode) {
-  StageLayout s{};
-  size_t o = 0;
-  s.tm = o; o += sizeof(float) * (size_t)K;
-  s.kidx = o; o += sizeof(int) * (size_t)(kKidxMax + 2);
-  s.thr = o; o += sizeof(float) * (size_t)L * 3 * (R + 1);
-  s.child = s.tile = s.prefix = s.nstate = s.nsuper = o;
-  if (mode != kModeDense) {
-    s.child = o; o += 4 * (size_t)nodes * kNodeWords;
-    s.tile = o; o += 4 * (size_t)nodes * kNodeWords;
-    s.prefix = o; o += 4 * (size_t)nodes * kNodeWords;
-    s.nstate = o; o += 4 * (size_t)nodes;
-  }
-  if (mode == kModeVdbRefined) {
-    s.nsuper = o; o += 4 * (size_t)nodes * kSuperWords;
-  }
-  s.bytes = (o + 15) & ~(size_t)15;
-  return s;
-}
-
-constexpr size_t kMaxStageBytes = 96 * 1024;
-
-template <typename T>
-__device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, int64_t count) {
-  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
-}
-
-// Pass 1.  Persistent: each warp takes 32-ray tiles in order until none is
-// left, so a warp never waits for another.  Writes counts[r], nruns[r]
-// (saturated at 255) and the first kMaxRuns runs at runs[r + j * n].
-template <int kMode, bool kSm, bool kSkip>
-__global__ void __launch_bounds__(kWalkBS) walk_kernel(
-    const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
-    LatticeDev lat, int32_t* __restrict__ counts, uint8_t* __restrict__ nruns_out,
-    uint2* __restrict__ runs, int64_t* __restrict__ tile_sum, unsigned* __restrict__ tile_counter,
-    unsigned* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
-  Tabs tb = global_tabs(g);
-  LatticeDev ls = lat;
-  if constexpr (kSm) {
-    const int64_t nodes = (int64_t)g.L * g.N * g.N * g.N;
-    const StageLayout sl = stage_layout(lat.K, g.L, g.R, nodes, kMode);
-    float* s_tm = reinterpret_cast<float*>(smem + sl.tm);
-    int* s_kidx = reinterpret_cast<int*>(smem + sl.kidx);
-    float* s_thr = reinterpret_cast<float*>(smem + sl.thr);
-    stage_copy(s_tm, lat.tm, lat.K);
-    stage_copy(s_kidx, lat.kidx, (int64_t)h.NB + 2);
-    stage_copy(s_thr, g.thr, (int64_t)g.L * 3 * (g.R + 1));
-    ls.tm = s_tm;
-    ls.kidx = s_kidx;
-    tb.thr = s_thr;
-    if constexpr (kMode != kModeDense) {
-      uint32_t* s_child = reinterpret_cast<uint32_t*>(smem + sl.child);
-      uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + sl.tile);
-      uint32_t* s_prefix = reinterpret_cast<uint32_t*>(smem + sl.prefix);
-      uint32_t* s_nstate = reinterpret_cast<uint32_t*>(smem + sl.nstate);
-      stage_copy(s_child, g.child, nodes * kNodeWords);
-      stage_copy(s_tile, g.tile, nodes * kNodeWords);
-      stage_copy(s_prefix, g.prefix, nodes * kNodeWords);
-      stage_copy(s_nstate, g.nstate, nodes);
-      tb.child = s_child;
-      tb.tile = s_tile;
-      tb.prefix = s_prefix;
-      tb.nstate = s_nstate;
-    }
-    if constexpr (kMode == kModeVdbRefined) {
-      uint32_t* s_nsuper = reinterpret_cast<uint32_t*>(smem + sl.nsuper);
-      stage_copy(s_nsuper, g.nsuper, nodes * kSuperWords);
-      tb.nsuper = s_nsuper;
-    }
-    __syncthreads();
-  }
-  const int lane = threadIdx.x & 31;
-  const unsigned ntiles = (unsigned)((n + 31) / 32);
-  for (;;) {
-    unsigned tile = 0;
-    if (lane == 0) tile = atomicAdd(tile_counter, 1u);
-    tile = __shfl_sync(kFull, tile, 0);
-    if (tile >= ntiles) break;
-    const int64_t r = (int64_t)tile * 32 + lane;
-    int64_t c = 0;
-    if (r < n) {
-      Ray ray;
-      int nr = 0;
-      if (load_ray(ro, rd, r, ray))
-        c = walk<kMode, false, kSm, kSkip>(g, tb, ls, h, ray, runs + r, n, nr, 0, 0, 0, nullptr,
-                                          nullptr, nullptr, status);
-      counts[r] = (int32_t)c;
-      nruns_out[r] = (uint8_t)min(nr, 255);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-    if (lane == 0) tile_sum[tile] = c;
-  }
-}
-
 constexpr int kEmitWarps = 4;
 
 // Pass 2.  One warp per 32-ray tile, independent of every other warp: its
@@ -541,11 +437,6 @@ int finish(int64_t* hw, const char* header, int64_t capacity, int64_t* total_out
   return HDDA_OK;
 }
 
-int walk_mode(const hdda_grid* grid) {
-  if (grid->kind == HDDA_GRID_DENSE) return kModeDense;
-  return grid->refine ? kModeVdbRefined : kModeVdb;
-}
-
 // One-pass launch over scratch = [32-byte header | tile states]:
 // header = {tile counter u32, status u32, total i64}.
 int run_onepass(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
@@ -587,51 +478,6 @@ size_t twopass_scratch_bytes(int64_t n) {
          a256(sizeof(uint2) * kMaxRuns * (size_t)n);
 }
 
-struct WalkArgs {
-  const float* ro;
-  const float* rd;
-  int64_t n;
-  GridDev g;
-  LatticeDev lat;
-  int32_t* counts;
-  uint8_t* nruns;
-  uint2* runs;
-  int64_t* tile_sum;
-  unsigned* counter;
-  unsigned* status;
-};
-
-template <int kMode, bool kSm, bool kSkip>
-int launch_walk(const WalkArgs& w, size_t smem, cudaStream_t s) {
-  auto kern = walk_kernel<kMode, kSm, kSkip>;
-  if (smem > 48 * 1024)
-    HDDA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-  int dev = 0, sms = 0, per_sm = 0;
-  HDDA_CUDA_TRY(cudaGetDevice(&dev));
-  HDDA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  HDDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkBS, smem));
-  const int64_t want = (w.n + kWalkBS - 1) / kWalkBS;
-  const int64_t full = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-  const unsigned grid = (unsigned)(want < full ? want : full);
-  kern<<<grid, kWalkBS, smem, s>>>(w.ro, w.rd, w.n, w.g, w.lat, w.counts, w.nruns, w.runs,
-                                   w.tile_sum, w.counter, w.status);
-  HDDA_CUDA_TRY(cudaGetLastError());
-  return HDDA_OK;
-}
-
-template <int kMode>
-int launch_walk_mode(const WalkArgs& w, size_t stage_bytes, bool skip, cudaStream_t s) {
-  if (skip)
-    return stage_bytes <= kMaxStageBytes ? launch_walk<kMode, true, true>(w, stage_bytes, s)
-                                         : launch_walk<kMode, false, true>(w, 0, s);
-  return stage_bytes <= kMaxStageBytes ? launch_walk<kMode, true, false>(w, stage_bytes, s)
-                                       : launch_walk<kMode, false, false>(w, 0, s);
-}
-
-const char* walk_name(int mode) {
-  return mode == kModeDense ? "dense_walk" : mode == kModeVdb ? "hdda_walk_plain" : "hdda_walk";
-}
 const char* emit_name(int mode) {
   return mode == kModeDense ? "dense_emit" : mode == kModeVdb ? "hdda_emit_plain" : "hdda_emit";
 }

@@ -30,6 +30,7 @@ EXPORTED = [
     "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
     "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine", "hdda_batch_create",
     "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free", "hdda_grid_set_walk",
+    "hdda_render",
 ]
 
 
@@ -114,6 +115,7 @@ def load(path: str | None = None):
     lib.hdda_traverse_hdda.argtypes = trav
     lib.hdda_traverse_hdda_noalloc.argtypes = trav
     lib.hdda_composite.argtypes = [vp, vp, i64, vp, vp, vp, vp, i32, vp, vp]
+    lib.hdda_render.argtypes = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, i32, vp, vp, vp]
     lib.hdda_profiler_enable.argtypes = [i32]
     lib.hdda_profiler_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
     for name in EXPORTED:
@@ -323,6 +325,29 @@ def composite(rays_o, rays_d, samples: Samples, field, out: torch.Tensor | None 
     _check(load().hdda_composite(_ptr(ro), _ptr(rd), n, _ptr(samples.offsets), _ptr(samples.t0),
                                  _ptr(samples.t1), _ptr(f), int(f.shape[0]), _ptr(out),
                                  _stream(stream)))
+    return out
+
+
+def render(rays_o, rays_d, grid: Grid, params: Params, field, out: torch.Tensor | None = None,
+           status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Render-only path (hdda_render): the frame that traverse + composite would
+    give, without writing any sample.  A VDB grid is walked by HDDA, a dense
+    grid by dense DDA.  With `status` (a CUDA int32/uint32 tensor of one
+    element) the call does not synchronise and device status bits are ORed
+    into it; without it the call checks them before returning."""
+    ro = _cuda(rays_o, torch.float32, (-1, 3))
+    rd = _cuda(rays_d, torch.float32, (-1, 3))
+    f = _cuda(field, torch.float32, (-1, 8))
+    n = int(ro.shape[0])
+    if out is None:
+        out = torch.empty((n, 4), dtype=torch.float32, device=ro.device)
+    st = 0
+    if status is not None:
+        if not status.is_cuda or status.numel() < 1 or status.element_size() != 4:
+            raise ValueError("status must be a CUDA tensor of 4-byte elements")
+        st = status.data_ptr()
+    _check(load().hdda_render(_ptr(ro), _ptr(rd), n, grid.handle, ctypes.byref(params), _ptr(f),
+                              int(f.shape[0]), _ptr(out), st, _stream(stream)))
     return out
 
 
