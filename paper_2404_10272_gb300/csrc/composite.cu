@@ -25,11 +25,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
     const int64_t* __restrict__ offsets, const float* __restrict__ t0,
     const float* __restrict__ t1, const float* __restrict__ field, int G,
     float* __restrict__ rgba, bool count_evals) {
-  __shared__ BlobTables bt;
-  __shared__ uint16_t s_list[kWarpsPerCta][kMaxGauss];  // blobs kept for the current chunk
+  extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kWarpsPerCta)
   __shared__ float s_T[kWarpsPerCta][32];
   __shared__ float4 s_C[kWarpsPerCta][32];
-  stage_blobs(bt, field, G);
+  const FieldSmem fs = stage_blobs(smem, field, G);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* T_s = s_T[wib];
@@ -55,9 +54,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
     __syncwarp();
     const int64_t wbeg = __shfl_sync(kFull, sb, 0);
     const int64_t wend = __shfl_sync(kFull, se, 31);
+    // the next chunk's interval ends are loaded one chunk ahead, so their
+    // DRAM latency overlaps the current chunk's field evaluation
+    float n0 = 0.f, n1 = 0.f;
+    if (wbeg + lane < wend) {
+      n0 = __ldg(t0 + wbeg + lane);
+      n1 = __ldg(t1 + wbeg + lane);
+    }
     for (int64_t base = wbeg; base < wend; base += 32) {
       const int64_t p = base + lane;
       const bool live = p < wend;
+      const float c0 = n0, c1 = n1;
+      if (p + 32 < wend) {
+        n0 = __ldg(t0 + p + 32);
+        n1 = __ldg(t1 + p + 32);
+      }
       int own = 0;  // the last lane whose first sample is <= p
 #pragma unroll
       for (int s = 16; s > 0; s >>= 1) {
@@ -70,15 +81,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
                   dz = __shfl_sync(kFull, d[2], own);
       float a0 = 0.f, a1 = 0.f, px = 0.f, py = 0.f, pz = 0.f;
       if (live) {
-        a0 = __ldg(t0 + p);
-        a1 = __ldg(t1 + p);
+        a0 = c0;
+        a1 = c1;
         const float tm = 0.5f * (a0 + a1);
         px = fmaf(tm, dx, ox);
         py = fmaf(tm, dy, oy);
         pz = fmaf(tm, dz, oz);
       }
-      composite_chunk(bt, G, s_list[wib], live, p + 1 >= wend, own, px, py, pz, a0, a1, T_s,
-                      C_s, evals);
+      composite_chunk(fs, G, live, p + 1 >= wend, own, px, py, pz, a0, a1, T_s, C_s, evals);
     }
     if (has_ray) {
       const float4 acc = C_s[lane];
@@ -117,7 +127,8 @@ extern "C" int hdda_composite(const float* rays_o, const float* rays_d, int64_t 
   if (blocks > INT32_MAX) return set_error(HDDA_ERR_INVALID_ARG, "too many rays");
   const unsigned grid = (unsigned)blocks;
   KernelTimer kt("composite", (cudaStream_t)stream);
-  composite_kernel<<<grid, kWarpsPerCta * 32, 0, (cudaStream_t)stream>>>(
+  composite_kernel<<<grid, kWarpsPerCta * 32, field_smem_bytes(n_gauss, kWarpsPerCta),
+                     (cudaStream_t)stream>>>(
       rays_o, rays_d, n_rays, offsets, t0, t1, field, n_gauss, rgba_out, profiler_on());
   kt.stop();
   HDDA_CUDA_TRY(cudaGetLastError());

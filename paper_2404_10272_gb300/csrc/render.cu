@@ -38,13 +38,12 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     LatticeDev lat, const uint8_t* __restrict__ nruns, const uint2* __restrict__ runs,
     const float* __restrict__ field, int G, float* __restrict__ rgba,
     unsigned* __restrict__ status, bool count_evals) {
-  __shared__ BlobTables bt;
-  __shared__ uint16_t s_list[kRenderWarps][kMaxGauss];
+  extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kRenderWarps)
   __shared__ float s_T[kRenderWarps][32];
   __shared__ float4 s_C[kRenderWarps][32];
   // run j of ray slot i at [j * kRenderRays + i]: {first k, first position}
   __shared__ uint2 s_run[kRenderWarps][kMaxRuns * kRenderRays];
-  stage_blobs(bt, field, G);
+  const FieldSmem fs = stage_blobs(smem, field, G);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t task = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -122,8 +121,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
         py = fmaf(tm, dy, oy);
         pz = fmaf(tm, dz, oz);
       }
-      composite_chunk(bt, G, s_list[wib], live, p + 1 >= W, own, px, py, pz, a0, a1, T_s, C_s,
-                      evals);
+      composite_chunk(fs, G, live, p + 1 >= W, own, px, py, pz, a0, a1, T_s, C_s, evals);
     }
     const bool more = k_next < lat.K;
     if (!__any_sync(kFull, more)) break;
@@ -192,17 +190,18 @@ int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* 
     const int64_t warps = (n + kRenderRays - 1) / kRenderRays;
     const unsigned nb = (unsigned)((warps + kRenderWarps - 1) / kRenderWarps);
     const bool ev = profiler_on();
+    const size_t fsm = field_smem_bytes(G, kRenderWarps);
     switch (mode) {
       case kModeDense:
-        render_kernel<kModeDense><<<nb, kRenderWarps * 32, 0, s>>>(
+        render_kernel<kModeDense><<<nb, kRenderWarps * 32, fsm, s>>>(
             ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
         break;
       case kModeVdb:
-        render_kernel<kModeVdb><<<nb, kRenderWarps * 32, 0, s>>>(
+        render_kernel<kModeVdb><<<nb, kRenderWarps * 32, fsm, s>>>(
             ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
         break;
       default:
-        render_kernel<kModeVdbRefined><<<nb, kRenderWarps * 32, 0, s>>>(
+        render_kernel<kModeVdbRefined><<<nb, kRenderWarps * 32, fsm, s>>>(
             ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
         break;
     }
