@@ -395,21 +395,31 @@ int hdda_render(const float* rays_o, const float* rays_d, int64_t n_rays,
                 int n_gauss, float* rgba_out, uint32_t* dev_status, hdda_stream_t stream);
 
 /*
- * Kernel timing for measurement.  While enabled, every kernel the library
- * launches is bracketed by two CUDA events recorded on the stream it is
- * launched on.  hdda_profiler_read synchronises on those events, writes up
- * to `cap` per-kernel aggregates (HOST array) and clears them; *n_out
- * (HOST) receives how many kernels were seen.  Adds one event pair per
- * launch; meant for benchmarks, off by default.  The paper has no
- * counterpart (it reports frame rates only).
+ * Kernel timing and work counters for measurement, off by default; the
+ * paper has no counterpart (it reports frame rates only).
+ *   HDDA_PROFILE_TIMERS    every kernel the library launches is bracketed
+ *                          by two CUDA events recorded on its stream (one
+ *                          event pair per launch)
+ *   HDDA_PROFILE_COUNTERS  the compositors count blob evaluations (sample x
+ *                          kept blob), one atomic add per warp task; this
+ *                          is extra device work, so time with the timers
+ *                          alone
+ * hdda_profiler_enable(flags) sets both switches (0 turns everything off).
+ * hdda_profiler_read synchronises on the recorded events, writes up to `cap`
+ * per-kernel aggregates (HOST array) and clears them; *n_out (HOST)
+ * receives how many entries there were.  Counters appear as entries named
+ * "composite_blob_evals" and "render_blob_evals" whose `launches` field
+ * holds the count and whose total_ms is 0.
  */
+enum { HDDA_PROFILE_TIMERS = 1, HDDA_PROFILE_COUNTERS = 2 };
+
 typedef struct {
     char name[48];
     int64_t launches;
     double total_ms;
 } hdda_kernel_time;
 
-int hdda_profiler_enable(int on);
+int hdda_profiler_enable(int flags);
 int hdda_profiler_read(hdda_kernel_time* out, int cap, int* n_out);
 
 #ifdef __cplusplus

@@ -98,14 +98,15 @@ __device__ __forceinline__ float warp_max(float v) {
 // One 32-sample chunk.  Lane `lane` holds a sample when `live`: the interval
 // [a0, a1) of the ray in slot `own`, evaluated at point (px, py, pz).  Live
 // lanes come first and are in ray order; `last` marks the lane holding the
-// warp's final sample.  Updates T_s[own] and C_s[own].  `evals`, when
-// non-null, counts sample x kept-blob evaluations.
-__device__ __forceinline__ void composite_chunk(const FieldSmem& fs, int G, bool live, bool last,
-                                                int own, float px, float py, float pz, float a0,
-                                                float a1, float* T_s, float4* C_s,
-                                                unsigned long long* evals) {
+// warp's final sample.  Updates T_s[own] and C_s[own].  Returns the
+// chunk's blob evaluations (live samples x kept blobs), the same on every
+// lane.
+__device__ __forceinline__ int composite_chunk(const FieldSmem& fs, int G, bool live, bool last,
+                                               int own, float px, float py, float pz, float a0,
+                                               float a1, float* T_s, float4* C_s) {
   const int lane = threadIdx.x & 31;
   float alpha = 0.f, wr = 0.f, wgr = 0.f, wb = 0.f;
+  int nevals;
   {
     // bounding box of the chunk's points, then the blobs within reach of it
     const float bx0 = warp_min(live ? px : INFINITY), by0 = warp_min(live ? py : INFINITY),
@@ -129,10 +130,7 @@ __device__ __forceinline__ void composite_chunk(const FieldSmem& fs, int G, bool
       if (near) kept[m + __popc(ball & ((1u << lane) - 1u))] = b;
       m += __popc(ball);
     }
-    if (evals) {
-      const int nl = __popc(__ballot_sync(kFieldFull, live));
-      if (lane == 0) atomicAdd(evals, (unsigned long long)m * (unsigned long long)nl);
-    }
+    nevals = m * __popc(__ballot_sync(kFieldFull, live));
     __syncwarp();
     float sigma = 0.f, sr = 0.f, sg = 0.f, sbl = 0.f;
 #pragma unroll 4
@@ -202,6 +200,7 @@ __device__ __forceinline__ void composite_chunk(const FieldSmem& fs, int G, bool
     C_s[own] = acc;
   }
   __syncwarp();
+  return nevals;
 }
 
 }  // namespace

@@ -114,8 +114,10 @@ int set_error(int code, const char* fmt, ...);
 int cuda_error(cudaError_t e, const char* what);
 void clear_error();
 
-// True while the kernel profiler is enabled (runtime.cu).
+// True while the kernel timers are enabled (runtime.cu).
 bool profiler_on();
+// True while the work counters are enabled (runtime.cu).
+bool counters_on();
 // Blob evaluations counted by the compositor since the last call (composite.cu).
 unsigned long long composite_take_blob_evals();
 // The same count for the render-only path (render.cu).

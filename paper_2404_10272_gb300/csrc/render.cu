@@ -5,8 +5,8 @@
 //
 // Pass 1 is the samplers' walk (walk_kernel, walk.cuh): each ray's merged
 // occupied runs of lattice indices [k_begin, k_end), the first kMaxRuns of
-// them, and its number of runs.  Pass 2 (render_kernel) gives each warp 16
-// consecutive rays, as the compositor over stored samples does.  Every
+// them, and its number of runs.  Pass 2 (render_kernel) gives each warp 8
+// consecutive rays (measured faster than 4 or 16).  Every
 // lattice index k of a run is the sample (t_k, t_{k+1}) with midpoint tm_k,
 // read from the lattice table all rays share, so a warp numbers its rays'
 // samples locally (a warp scan of the run lengths), and lane j of each
@@ -26,7 +26,7 @@ namespace hdda {
 namespace {
 
 constexpr int kRenderWarps = 4;
-constexpr int kRenderRays = 16;  // rays per warp task
+constexpr int kRenderRays = 8;  // rays per warp task
 constexpr uint32_t kNoRun = 0x7fffffffu;
 
 // Blob evaluations (sample x kept blob), counted only while profiling.
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   float* T_s = s_T[wib];
   float4* C_s = s_C[wib];
   uint2* sr = s_run[wib];
-  unsigned long long* evals = count_evals ? &g_render_evals : nullptr;
+  unsigned long long evals = 0;  // this warp's blob evaluations
   const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
   const int64_t r = task * kRenderRays + lane;
   const bool has_ray = lane < kRenderRays && r < n;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
         py = fmaf(tm, dy, oy);
         pz = fmaf(tm, dz, oz);
       }
-      composite_chunk(fs, G, live, p + 1 >= W, own, px, py, pz, a0, a1, T_s, C_s, evals);
+      evals += composite_chunk(fs, G, live, p + 1 >= W, own, px, py, pz, a0, a1, T_s, C_s);
     }
     const bool more = k_next < lat.K;
     if (!__any_sync(kFull, more)) break;
@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     const float4 acc = C_s[lane];
     reinterpret_cast<float4*>(rgba)[r] = make_float4(acc.x, acc.y, acc.z, 1.f - T_s[lane]);
   }
+  if (count_evals && lane == 0) atomicAdd(&g_render_evals, evals);
 }
 
 const char* render_name(int mode) {
@@ -189,7 +190,7 @@ int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* 
     KernelTimer kt(render_name(mode), s);
     const int64_t warps = (n + kRenderRays - 1) / kRenderRays;
     const unsigned nb = (unsigned)((warps + kRenderWarps - 1) / kRenderWarps);
-    const bool ev = profiler_on();
+    const bool ev = counters_on();
     const size_t fsm = field_smem_bytes(G, kRenderWarps);
     switch (mode) {
       case kModeDense:

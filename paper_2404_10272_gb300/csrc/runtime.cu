@@ -36,7 +36,8 @@ struct ProfRecord {
   cudaEvent_t a, b;
 };
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+bool g_prof_on = false;        // kernel timers
+bool g_count_on = false;       // work counters
 std::vector<ProfRecord> g_prof_records;
 std::vector<cudaEvent_t> g_prof_pool;
 
@@ -55,6 +56,11 @@ cudaEvent_t take_event() {
 bool profiler_on() {
   std::lock_guard<std::mutex> lock(g_prof_mu);
   return g_prof_on;
+}
+
+bool counters_on() {
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  return g_count_on;
 }
 
 KernelTimer::KernelTimer(const char* name, cudaStream_t s, bool allow) : name_(name), s_(s) {
@@ -84,9 +90,10 @@ extern "C" const char* hdda_version(void) { return "hdda 0.1 (sm_103a)"; }
 
 extern "C" const char* hdda_last_error(void) { return hdda::g_last_error; }
 
-extern "C" int hdda_profiler_enable(int on) {
+extern "C" int hdda_profiler_enable(int flags) {
   std::lock_guard<std::mutex> lock(hdda::g_prof_mu);
-  hdda::g_prof_on = on != 0;
+  hdda::g_prof_on = (flags & HDDA_PROFILE_TIMERS) != 0;
+  hdda::g_count_on = (flags & HDDA_PROFILE_COUNTERS) != 0;
   return HDDA_OK;
 }
 

@@ -351,8 +351,15 @@ def render(rays_o, rays_d, grid: Grid, params: Params, field, out: torch.Tensor 
     return out
 
 
-def profiler_enable(on: bool = True):
-    _check(load().hdda_profiler_enable(1 if on else 0))
+PROFILE_TIMERS = 1
+PROFILE_COUNTERS = 2
+
+
+def profiler_enable(on: bool = True, counters: bool = False):
+    """Kernel timers on or off; `counters` also turns on the work counters
+    (extra device work: time with the timers alone)."""
+    flags = (PROFILE_TIMERS if on else 0) | (PROFILE_COUNTERS if counters else 0)
+    _check(load().hdda_profiler_enable(flags))
 
 
 def profiler_read() -> dict:

@@ -170,3 +170,31 @@ def test_edges(H):
     assert float(H.render(ot, dt, g, prm, z).abs().max()) == 0.0
     with pytest.raises(H.HddaError):
         H.render(ot, dt, g, prm, torch.zeros((257, 8), dtype=torch.float32, device="cuda"))
+
+
+def test_counters_leave_pixels_unchanged(H):
+    sc = scenes.tiny_scene()
+    o, d = scenes.tiny_camera().rays()
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    f = torch.from_numpy(sc.field).cuda()
+    g = H.build_vdb(torch.from_numpy(sc.occ).cuda(), sc.aabbs)
+    prm = _params(H, sc.params)
+    plain = to_np(H.render(ot, dt, g, prm, f))
+    s = H.traverse_hdda(ot, dt, g, prm)
+    comp = to_np(H.composite(ot, dt, s, f))
+    H.profiler_read()
+    H.profiler_enable(True, counters=True)
+    try:
+        counted = to_np(H.render(ot, dt, g, prm, f))
+        counted_c = to_np(H.composite(ot, dt, s, f))
+    finally:
+        H.profiler_enable(False)
+    got = H.profiler_read()
+    assert np.array_equal(counted.view(np.uint32), plain.view(np.uint32))
+    assert np.array_equal(counted_c.view(np.uint32), comp.view(np.uint32))
+    # culling keeps at most every blob for every sample
+    n_samples = s.total
+    for name in ("render_blob_evals", "composite_blob_evals"):
+        ev = got[name][0]
+        assert 0 < ev <= n_samples * sc.field.shape[0], (name, ev)
+    assert got["hdda_render"][0] == 1 and got["composite"][0] == 1
