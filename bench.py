@@ -63,7 +63,7 @@ def parse_args():
                          "the default line); batch: 64 mixed jobs in one graph launch against 64 "
                          "separate launches; serve: continuous-batching render server under "
                          "Poisson load")
-    ap.add_argument("--profile-step", choices=["hdda", "dense"], default=None,
+    ap.add_argument("--profile-step", choices=["hdda", "dense", "render"], default=None,
                     help="profiling aid: one count-only call, one warm-up step and one step of "
                          "the given path on camera 0, no timing, no JSON line")
     return ap.parse_args()
@@ -561,7 +561,7 @@ def profile_step(args):
     field = torch.from_numpy(sc.field).cuda()
     p = sc.params
     prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
-    vdb = args.profile_step == "hdda"
+    vdb = args.profile_step in ("hdda", "render")
     grid = hdda.build_vdb(dense, sc.aabbs) if vdb else hdda.pack_dense(dense, sc.aabbs)
     trav = hdda.traverse_hdda if vdb else hdda.traverse_dense
     cap = trav(O, D, grid, prm, count_only=True).total
@@ -571,6 +571,13 @@ def profile_step(args):
         grid.rebuild(dense)
         s = trav(O, D, grid, prm, out=bufs)
         hdda.composite(O, D, s, field, out=rgba)
+    if args.profile_step == "render":
+        # then the render-only step twice: rebuild, walk, run-level compositing
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            grid.rebuild(dense)
+            hdda.render(O, D, grid, prm, field, out=rgba, status=status)
+        assert int(status.item()) == 0
     torch.cuda.synchronize()
     print(f"profile step done: {o.shape[0]} rays, {s.total} samples")
 

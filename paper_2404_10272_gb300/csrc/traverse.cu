@@ -33,11 +33,11 @@
 // (persistent warps take 32-ray tiles in order from an atomic counter and
 // walk them with the lattice, bucket, threshold and node tables staged in
 // shared memory; each ray's sample count and merged occupied runs go to
-// global memory, with no CTA barrier anywhere) and emit_kernel (each CTA
-// loads 128 counts, publishes their sum at once and finds its output offset
-// by a decoupled look-back over earlier tiles, writes the CSR offsets, and
-// every warp expands its rays' runs into (ray, t_k, t_k+1) samples with
-// coalesced stores).  The allocation-free entry point runs one kernel,
+// global memory, with no CTA barrier anywhere, plus one sum per 32-ray
+// tile), tile_scan_kernel (one CTA scans the tile sums), and emit_kernel
+// (one warp per tile: its offset is the tile's prefix plus a warp scan; it
+// writes the CSR offsets and expands its rays' runs into (ray, t_k,
+// t_k+1) samples with coalesced 16-byte stores, four samples per lane).  The allocation-free entry point runs one kernel,
 // onepass_kernel, whose CTAs keep the runs in shared memory and look back
 // right after walking, so its scratch stays a few hundred kilobytes.  A ray
 // with more runs than are kept walks again and writes its own samples.
@@ -265,8 +265,9 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
     LatticeDev lat, const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
     const uint2* __restrict__ runs, const int64_t* __restrict__ tile_prefix,
     int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
-    float* __restrict__ t1, int64_t capacity, unsigned* __restrict__ status) {
+    float* __restrict__ t1, int64_t capacity, bool vec, unsigned* __restrict__ status) {
   __shared__ uint2 s_runs[kEmitWarps][kMaxRuns * 32];  // run j of lane i at [j * 32 + i]
+  __shared__ int64_t s_end[kEmitWarps][32];            // end position of lane i's samples
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = (int64_t)blockIdx.x * kEmitWarps + warp;
   if (tile * 32 >= n) return;  // uniform per warp
@@ -290,8 +291,15 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
   if (r < n) offsets[r] = off;
   if (capacity <= 0) return;
   const bool overflow = nr > kMaxRuns;
-  expand_warp<true>(off, c, overflow, my_runs, 32, (int32_t)(tile * 32), lat.t, capacity, ray_idx,
-                    t0, t1);
+  if (vec) {
+    s_end[warp][lane] = off + c;
+    __syncwarp();
+    expand_warp_v4<true>(off, c, overflow, my_runs, 32, (int32_t)(tile * 32), s_end[warp], lat.t,
+                         capacity, ray_idx, t0, t1);
+  } else {
+    expand_warp<true>(off, c, overflow, my_runs, 32, (int32_t)(tile * 32), lat.t, capacity,
+                      ray_idx, t0, t1);
+  }
   if (overflow) {
     Ray ray;
     load_ray(ro, rd, r, ray);
@@ -524,21 +532,23 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   {
     KernelTimer kt(emit_name(mode), s);
     const unsigned nb = (unsigned)((T + kEmitWarps - 1) / kEmitWarps);
+    const bool vec = ((reinterpret_cast<uintptr_t>(ray_idx) | reinterpret_cast<uintptr_t>(t0) |
+                       reinterpret_cast<uintptr_t>(t1)) & 15) == 0;
     switch (mode) {
       case kModeDense:
         emit_kernel<kModeDense><<<nb, kEmitWarps * 32, 0, s>>>(
             ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, status);
+            capacity, vec, status);
         break;
       case kModeVdb:
         emit_kernel<kModeVdb><<<nb, kEmitWarps * 32, 0, s>>>(
             ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, status);
+            capacity, vec, status);
         break;
       default:
         emit_kernel<kModeVdbRefined><<<nb, kEmitWarps * 32, 0, s>>>(
             ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, status);
+            capacity, vec, status);
         break;
     }
   }

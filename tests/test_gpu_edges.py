@@ -94,3 +94,42 @@ def test_degenerate_rays(H):
     ref = _check(H, occ, aabbs, o, d, p, "degenerate")
     cnt = np.diff(ref[0])
     assert cnt[0] == 0 and cnt[1] == 128 and cnt[5] == 0   # all or nothing for zero directions
+
+
+def test_output_alignment_and_capacity_residues(H):
+    """Sample buffers that are not 16-byte aligned take the element-wise
+    emit; capacities of every residue mod 4 end the 16-byte stores exactly at
+    capacity on both paths."""
+    sc = scenes.tiny_scene()
+    o, d = scenes.tiny_camera().rays()
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    g = H.build_vdb(torch.from_numpy(sc.occ).cuda(), sc.aabbs)
+    p = sc.params
+    prm = H.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    full = H.traverse_hdda(ot, dt, g, prm)
+    ref = tuple(x.detach().cpu().numpy() for x in full.trimmed())
+    assert full.total > 200
+    n = o.shape[0]
+    for shift in (0, 1, 2, 3):          # element offset of the views: 0 = 16-byte aligned
+        for cap in (full.total, full.total - 37, full.total - 38, full.total - 39, full.total - 40):
+            buf = H.alloc_samples(n, cap + 8)
+            buf.ray_idx.fill_(-7)
+            buf.t0.fill_(-1.0)
+            buf.t1.fill_(-1.0)
+            view = H.Samples(buf.offsets, buf.ray_idx[shift:shift + cap],
+                             buf.t0[shift:shift + cap], buf.t1[shift:shift + cap], 0)
+            if cap == full.total:
+                got = H.traverse_hdda(ot, dt, g, prm, out=view)
+                assert_same(tuple(x.detach().cpu().numpy() for x in got.trimmed()), ref,
+                            f"shift {shift}")
+            else:
+                with pytest.raises(H.HddaError) as ex:
+                    H.traverse_hdda(ot, dt, g, prm, out=view)
+                assert ex.value.code == H.ERR_CAPACITY
+                got_t0 = buf.t0[shift:shift + cap].cpu().numpy()
+                assert np.array_equal(got_t0.view(np.uint32), ref[2][:cap].view(np.uint32))
+                assert np.array_equal(buf.ray_idx[shift:shift + cap].cpu().numpy(), ref[1][:cap])
+            # nothing before the view or at or past its capacity
+            for arr, fill in ((buf.ray_idx, -7), (buf.t0, -1.0), (buf.t1, -1.0)):
+                a = arr.cpu().numpy()
+                assert np.all(a[:shift] == fill) and np.all(a[shift + cap:] == fill)
