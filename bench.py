@@ -43,9 +43,10 @@ L2_FLUSH_BYTES = 256 << 20
 # does in a separate untimed pass.
 COMPOSITE_FP32_PER_BLOB = 11
 KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
-# DRAM bytes (read + write) per launch from ncu --set full of the object-centric step, for the
+# DRAM bytes (read + write) per launch from ncu --set full of the object-centric step on
+# camera 0 (the capture commands are kept with the profile summaries), for the
 # roofline's "traffic"; an entry must be dropped whenever its kernel changes.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {"composite": 236_723_968, "hdda_emit": 269_825_280, "hdda_walk": 15_879_168}
 
 
 def parse_args():
@@ -356,7 +357,11 @@ def run_ours(args):
     S_avg = samples / K
     grid_bytes = int(vstats.bytes)
     G = int(sc.field.shape[0])
-    # algorithmic bytes (or FP32 instructions) per launch: see DESIGN.md, "Roofline"
+    # algorithmic bytes per launch: what each kernel must move at least.  Walk: the rays
+    # (24 B each) and the grid once.  Emit: the CSR offsets (8 B per ray) and the samples
+    # (ray_idx, t0, t1: 12 B each).  Compositor: rays, offsets, t0/t1 (8 B per sample),
+    # the pixels (16 B per ray) and the field.  The sampler as a whole: rays in, offsets
+    # and samples out, grid once.
     sampler_bytes = 24 * n + 8 * (n + 1) + 12 * S_avg + grid_bytes
     alg_bytes = {
         "hdda_walk": 24 * n + grid_bytes,
@@ -548,7 +553,8 @@ def run_reference(args):
 
 def profile_step(args):
     """Kernel launch order: sample (count only), build, sample, composite (warm-up),
-    build, sample, composite (the step to capture)."""
+    build, sample, composite (the step to capture).  For "render": build, render
+    (warm-up), build, render."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -564,20 +570,23 @@ def profile_step(args):
     vdb = args.profile_step in ("hdda", "render")
     grid = hdda.build_vdb(dense, sc.aabbs) if vdb else hdda.pack_dense(dense, sc.aabbs)
     trav = hdda.traverse_hdda if vdb else hdda.traverse_dense
-    cap = trav(O, D, grid, prm, count_only=True).total
-    bufs = hdda.alloc_samples(o.shape[0], cap)
     rgba = torch.empty((o.shape[0], 4), dtype=torch.float32, device="cuda")
-    for _ in range(2):
-        grid.rebuild(dense)
-        s = trav(O, D, grid, prm, out=bufs)
-        hdda.composite(O, D, s, field, out=rgba)
     if args.profile_step == "render":
-        # then the render-only step twice: rebuild, walk, run-level compositing
+        # the render-only step twice: rebuild, walk, run-level compositing
         status = torch.zeros(1, dtype=torch.int32, device="cuda")
         for _ in range(2):
             grid.rebuild(dense)
             hdda.render(O, D, grid, prm, field, out=rgba, status=status)
+        torch.cuda.synchronize()
         assert int(status.item()) == 0
+        print(f"profile step done: {o.shape[0]} rays, render only")
+        return
+    cap = trav(O, D, grid, prm, count_only=True).total
+    bufs = hdda.alloc_samples(o.shape[0], cap)
+    for _ in range(2):
+        grid.rebuild(dense)
+        s = trav(O, D, grid, prm, out=bufs)
+        hdda.composite(O, D, s, field, out=rgba)
     torch.cuda.synchronize()
     print(f"profile step done: {o.shape[0]} rays, {s.total} samples")
 
