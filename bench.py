@@ -661,15 +661,17 @@ def run_batch(args):
                                "cascade levels, images uniform 64..800 per side (seed 1004)",
                    "rays_per_step": n_rays, "samples_per_step": int(samples),
                    "autotuned": {"walk_block": best[0], "rays_per_fetch": best[1],
-                                 "emit_warps": best[2]},
+                                 "emit_warps": best[2],
+                                 "walk_form": "skip" if len(best) > 3 and best[3] else "branch"},
                    "l2": "not flushed: 64 jobs' outputs exceed the L2 each step"},
         "samples_per_s": round(samples / (ms_batch / 1e3), 1),
         "separate_launches": {"ms_per_step": round(ms_sep, 4),
                               "rays_per_s": round(n_rays / (ms_sep / 1e3), 1)},
         "speedup_vs_separate": round(ms_sep / ms_batch, 3),
         "autotune": {"seconds": round(t_tune, 2), "candidates": len(timings),
-                     "median_ms": {f"{k[0]}/{k[1]}/{k[2]}": round(sorted(v)[len(v) // 2], 4)
-                                   for k, v in sorted(timings.items())}},
+                     "median_ms": {"/".join(str(x) for x in k): round(sorted(v)[len(v) // 2], 4)
+                                   for k, v in sorted(timings.items())},
+                     "key": "walk_block/rays_per_fetch/emit_warps/walk_variant (1 = skip)"},
         "clocks": clk,
     }), flush=True)
     b.free()

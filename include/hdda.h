@@ -323,12 +323,15 @@ typedef struct {
     int rays_per_fetch;  /* rays a warp takes per atomic fetch: 32..1024, x32 */
     int emit_warps;      /* warps (32-ray tiles) per CTA of the emit: 2, 4, 8 */
     int use_graph;       /* capture the sequence in a CUDA graph at create    */
+    int walk_variant;    /* HDDA_WALK_BRANCH or HDDA_WALK_SKIP: the control
+                            flow of Algorithm 1 or of Algorithm 2; both keep
+                            the same samples                                  */
 } hdda_batch_config;
 
 typedef struct hdda_batch hdda_batch;  /* opaque, library-owned */
 
 /* Builds a batch plan for `n_jobs` jobs (HOST array, 1..4096); cfg (HOST) may
- * be NULL for {256, 64, 4, 1}.  Looks up each job's lattice (synchronising
+ * be NULL for {256, 64, 4, 1, HDDA_WALK_BRANCH}.  Looks up each job's lattice (synchronising
  * once per new parameter set) and synchronises the stream once. */
 int hdda_batch_create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg,
                       hdda_batch** out, hdda_stream_t stream);

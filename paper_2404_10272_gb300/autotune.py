@@ -1,13 +1,16 @@
 """Autotuner for the batched sampler's launch shape.
 
-It chooses three sizes of `hdda_batch_config` for a given batch by timing:
+It chooses the fields of `hdda_batch_config` for a given batch by timing:
 * the walk's threads per CTA;
 * the rays a warp takes per work-stealing fetch;
-* the 32-ray tiles per CTA of the emit.
+* the 32-ray tiles per CTA of the emit;
+* then, at the best of those launch shapes, the walk's control flow:
+  Algorithm 1's branch form or Algorithm 2's skip form (same samples).
 
 Every candidate builds its own plan, whose CUDA graph is captured once. It is
 launched a few times untimed, then timed over `reps` launches with CUDA events.
-The candidate with the smallest median wins.
+The candidate with the smallest median wins.  Configurations are 4-tuples
+(walk_block, rays_per_fetch, emit_warps, walk_variant).
 
 Results are cached in a JSON file keyed by the device name and a signature of
 the workload. The file is `$HDDA_AUTOTUNE_CACHE` if set, else `autotune.json`
@@ -23,7 +26,9 @@ from typing import Callable, Iterable
 WALK_BLOCKS = (128, 256, 512)
 RAYS_PER_FETCH = (32, 64, 128)
 EMIT_WARPS = (2, 4, 8)
-SPACE = [(wb, rpf, ew) for wb in WALK_BLOCKS for rpf in RAYS_PER_FETCH for ew in EMIT_WARPS]
+WALK_BRANCH, WALK_SKIP = 0, 1   # hdda_walk_variant
+SPACE = [(wb, rpf, ew, WALK_BRANCH) for wb in WALK_BLOCKS for rpf in RAYS_PER_FETCH
+         for ew in EMIT_WARPS]
 
 
 def cache_path() -> str:
@@ -63,11 +68,9 @@ def store_cache(key: str, value: dict, path: str | None = None) -> None:
 
 
 def choose(timings: dict) -> tuple:
-    """The configuration with the smallest median time (ties: the first in SPACE order)."""
+    """The configuration with the smallest median time (ties: the first timed)."""
     best = None
-    for cfg in SPACE:
-        if cfg not in timings:
-            continue
+    for cfg in timings:
         med = statistics.median(timings[cfg])
         if best is None or med < best[1]:
             best = (cfg, med)
@@ -113,6 +116,10 @@ def tune(make_batch: Callable, key: str, space: Iterable[tuple] = SPACE, reps: i
             return tuple(hit["config"]), {tuple(json.loads(k)): v for k, v in hit["timings"].items()}
     timer = timer or time_config
     timings = {tuple(cfg): timer(make_batch, tuple(cfg), reps, warmup) for cfg in space}
+    shape = choose(timings)
+    alt = shape[:3] + (WALK_SKIP if shape[3] == WALK_BRANCH else WALK_BRANCH,)
+    if alt not in timings:
+        timings[alt] = timer(make_batch, alt, reps, warmup)
     best = choose(timings)
     if use_cache:
         store_cache(full_key, {"config": list(best),

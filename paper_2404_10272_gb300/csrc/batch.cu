@@ -62,7 +62,7 @@ __device__ __forceinline__ void warp_copy_grid(GridDev* dst, const GridDev* src)
   __syncwarp();
 }
 
-template <int kMode, int kBlock>
+template <int kMode, int kBlock, bool kSkip>
 __global__ void __launch_bounds__(kBlock) batch_walk_kernel(
     const JobDev* __restrict__ jobs, const int64_t* __restrict__ tile0, int J, int64_t T,
     int tiles_per_fetch, int32_t* __restrict__ counts, uint8_t* __restrict__ nruns_out,
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(kBlock) batch_walk_kernel(
         Ray ray;
         int nr = 0;
         if (load_ray(ro, rd, lr, ray))
-          c = walk<kMode, false, false>(g, global_tabs(g), lat, h, ray, runs + gr, slots, nr, 0,
-                                        0, 0, nullptr, nullptr, nullptr, status);
+          c = walk<kMode, false, false, kSkip>(g, global_tabs(g), lat, h, ray, runs + gr, slots,
+                                               nr, 0, 0, 0, nullptr, nullptr, nullptr, status);
         counts[gr] = (int32_t)c;
         nruns_out[gr] = (uint8_t)min(nr, 255);
       }
@@ -212,40 +212,51 @@ struct hdda_batch {
 namespace hdda {
 namespace {
 
-template <int kMode, int kBlock>
+template <int kMode, int kBlock, bool kSkip>
 int batch_walk_grid(unsigned* out) {
   int dev = 0, sms = 0, per_sm = 0;
   HDDA_CUDA_TRY(cudaGetDevice(&dev));
   HDDA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HDDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, batch_walk_kernel<kMode, kBlock>, kBlock, 0));
+      &per_sm, batch_walk_kernel<kMode, kBlock, kSkip>, kBlock, 0));
   *out = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
   return HDDA_OK;
 }
 
-template <int kMode>
-int walk_grid_for_block(int block, unsigned* out) {
+template <int kMode, bool kSkip>
+int walk_grid_for(int block, unsigned* out) {
   switch (block) {
-    case 128: return batch_walk_grid<kMode, 128>(out);
-    case 256: return batch_walk_grid<kMode, 256>(out);
-    default: return batch_walk_grid<kMode, 512>(out);
+    case 128: return batch_walk_grid<kMode, 128, kSkip>(out);
+    case 256: return batch_walk_grid<kMode, 256, kSkip>(out);
+    default: return batch_walk_grid<kMode, 512, kSkip>(out);
   }
 }
 
 template <int kMode>
-void launch_batch_walk(const hdda_batch* b, cudaStream_t s) {
+int walk_grid_for_block(int block, bool skip, unsigned* out) {
+  return skip ? walk_grid_for<kMode, true>(block, out) : walk_grid_for<kMode, false>(block, out);
+}
+
+template <int kMode, bool kSkip>
+void launch_batch_walk_v(const hdda_batch* b, cudaStream_t s) {
   const unsigned grid = b->walk_grid;
   const int tpf = b->cfg.rays_per_fetch / 32;
-#define HDDA_BATCH_WALK(BS)                                                              \
-  batch_walk_kernel<kMode, BS><<<grid, BS, 0, s>>>(b->jobs, b->tile0, b->n_jobs, b->T,  \
-                                                   tpf, b->counts, b->nruns, b->runs,    \
-                                                   b->tile_sum, b->counter, b->status)
+#define HDDA_BATCH_WALK(BS)                                                                     \
+  batch_walk_kernel<kMode, BS, kSkip><<<grid, BS, 0, s>>>(b->jobs, b->tile0, b->n_jobs, b->T,  \
+                                                          tpf, b->counts, b->nruns, b->runs,    \
+                                                          b->tile_sum, b->counter, b->status)
   switch (b->cfg.walk_block) {
     case 128: HDDA_BATCH_WALK(128); break;
     case 256: HDDA_BATCH_WALK(256); break;
     default: HDDA_BATCH_WALK(512); break;
   }
 #undef HDDA_BATCH_WALK
+}
+
+template <int kMode>
+void launch_batch_walk(const hdda_batch* b, cudaStream_t s) {
+  if (b->cfg.walk_variant == HDDA_WALK_SKIP) launch_batch_walk_v<kMode, true>(b, s);
+  else launch_batch_walk_v<kMode, false>(b, s);
 }
 
 template <int kMode>
@@ -294,6 +305,8 @@ int check_config(const hdda_batch_config& c) {
     return set_error(HDDA_ERR_INVALID_ARG, "rays_per_fetch must be a multiple of 32 in 32..1024");
   if (c.emit_warps != 2 && c.emit_warps != 4 && c.emit_warps != 8)
     return set_error(HDDA_ERR_INVALID_ARG, "emit_warps must be 2, 4 or 8");
+  if (c.walk_variant != HDDA_WALK_BRANCH && c.walk_variant != HDDA_WALK_SKIP)
+    return set_error(HDDA_ERR_INVALID_ARG, "walk_variant must be HDDA_WALK_BRANCH or _SKIP");
   return HDDA_OK;
 }
 
@@ -304,7 +317,7 @@ int create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg, hdda_
   if (n_jobs < 1 || n_jobs > kMaxBatchJobs)
     return set_error(HDDA_ERR_INVALID_ARG, "n_jobs=%d outside 1..%d", n_jobs, kMaxBatchJobs);
   if (!jobs) return set_error(HDDA_ERR_INVALID_ARG, "jobs is NULL");
-  hdda_batch_config c{256, 64, 4, 1};
+  hdda_batch_config c{256, 64, 4, 1, HDDA_WALK_BRANCH};
   if (cfg) c = *cfg;
   int st = check_config(c);
   if (st != HDDA_OK) return st;
@@ -405,10 +418,17 @@ int create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg, hdda_
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables may go out of scope
   if (e != cudaSuccess) st = cuda_error(e, "batch tables");
   if (st == HDDA_OK) {
+    const bool skip = c.walk_variant == HDDA_WALK_SKIP;
     switch (mode) {
-      case kModeDense: st = walk_grid_for_block<kModeDense>(c.walk_block, &b->walk_grid); break;
-      case kModeVdb: st = walk_grid_for_block<kModeVdb>(c.walk_block, &b->walk_grid); break;
-      default: st = walk_grid_for_block<kModeVdbRefined>(c.walk_block, &b->walk_grid); break;
+      case kModeDense:
+        st = walk_grid_for_block<kModeDense>(c.walk_block, skip, &b->walk_grid);
+        break;
+      case kModeVdb:
+        st = walk_grid_for_block<kModeVdb>(c.walk_block, skip, &b->walk_grid);
+        break;
+      default:
+        st = walk_grid_for_block<kModeVdbRefined>(c.walk_block, skip, &b->walk_grid);
+        break;
     }
   }
   if (st == HDDA_OK && c.use_graph) {

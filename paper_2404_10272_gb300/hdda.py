@@ -64,7 +64,8 @@ class Job(ctypes.Structure):
 
 class BatchConfig(ctypes.Structure):
     _fields_ = [("walk_block", ctypes.c_int32), ("rays_per_fetch", ctypes.c_int32),
-                ("emit_warps", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("emit_warps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("walk_variant", ctypes.c_int32)]
 
 
 class GridStats(ctypes.Structure):
@@ -381,7 +382,8 @@ class Batch:
     jobs: list of dicts with rays_o, rays_d (CUDA float32 [n, 3]), grid (Grid),
     params (Params) and out (Samples: offsets [n+1] and sample buffers whose
     length is the job's capacity).  The tensors and grids are kept alive
-    by the batch.
+    by the batch.  config: (walk_block, rays_per_fetch, emit_warps[,
+    walk_variant]) with walk_variant WALK_BRANCH (default) or WALK_SKIP.
     """
 
     def __init__(self, jobs, config=DEFAULT_BATCH_CONFIG, use_graph=True, stream=None):
@@ -397,9 +399,10 @@ class Batch:
                          int(out.t0.numel()))
         self.n_jobs = len(jobs)
         self.jobs = jobs
-        wb, rpf, ew = config
-        cfg = BatchConfig(wb, rpf, ew, 1 if use_graph else 0)
-        self.config = (wb, rpf, ew)
+        wb, rpf, ew = config[:3]
+        wv = config[3] if len(config) > 3 else WALK_BRANCH
+        cfg = BatchConfig(wb, rpf, ew, 1 if use_graph else 0, wv)
+        self.config = (wb, rpf, ew, wv)
         h = ctypes.c_void_p()
         _check(load().hdda_batch_create(arr, self.n_jobs, ctypes.byref(cfg), ctypes.byref(h),
                                         _stream(stream)))

@@ -6,10 +6,11 @@ from paper_2404_10272_gb300 import autotune, scenes
 
 
 def test_choose_takes_smallest_median_and_first_on_ties():
-    t = {(256, 64, 4): [3.0, 1.0, 2.0], (128, 32, 2): [2.0, 2.0, 2.0], (512, 128, 8): [5, 5, 5]}
-    assert autotune.choose(t) == (128, 32, 2)      # medians 2.0 vs 2.0: SPACE order decides
-    t[(128, 32, 2)] = [2.5, 2.5, 2.5]
-    assert autotune.choose(t) == (256, 64, 4)
+    t = {(256, 64, 4, 0): [3.0, 1.0, 2.0], (128, 32, 2, 0): [2.0, 2.0, 2.0],
+         (512, 128, 8, 0): [5, 5, 5]}
+    assert autotune.choose(t) == (256, 64, 4, 0)   # medians 2.0 vs 2.0: the first timed wins
+    t[(256, 64, 4, 0)] = [2.5, 2.5, 2.5]
+    assert autotune.choose(t) == (128, 32, 2, 0)
     with pytest.raises(ValueError):
         autotune.choose({})
 
@@ -20,13 +21,14 @@ def test_tune_uses_timer_then_cache(tmp_path, monkeypatch):
 
     def fake_timer(make_batch, cfg, reps, warmup):
         calls.append(cfg)
-        wb, rpf, ew = cfg
-        return [abs(wb - 256) + abs(rpf - 64) + abs(ew - 4) + 1.0] * reps
+        wb, rpf, ew, wv = cfg
+        return [abs(wb - 256) + abs(rpf - 64) + abs(ew - 4) + 1.0 - 0.5 * wv] * reps
 
     best, timings = autotune.tune(None, "wl", timer=fake_timer, device_name="dev")
-    assert best == (256, 64, 4)
-    assert len(calls) == len(autotune.SPACE) == 27
-    assert set(timings) == set(autotune.SPACE)
+    # the launch shape first, then the control flow at that shape
+    assert best == (256, 64, 4, autotune.WALK_SKIP)
+    assert len(calls) == len(autotune.SPACE) + 1 == 28
+    assert set(timings) == set(autotune.SPACE) | {(256, 64, 4, autotune.WALK_SKIP)}
 
     def failing_timer(*a):
         raise AssertionError("the cache should have answered")
@@ -35,7 +37,7 @@ def test_tune_uses_timer_then_cache(tmp_path, monkeypatch):
     assert best2 == best and timings2 == timings
     # another device or workload is tuned afresh
     best3, _ = autotune.tune(None, "wl", timer=fake_timer, device_name="other")
-    assert best3 == best and len(calls) == 54
+    assert best3 == best and len(calls) == 56
 
 
 def test_batch_jobs_are_seeded_and_within_bounds():

@@ -52,7 +52,8 @@ def _jobs(H, specs, grids, fn, slack=0):
 
 
 @pytest.mark.parametrize("config,graph", [((256, 64, 4), True), ((128, 32, 2), False),
-                                          ((512, 128, 8), True)])
+                                          ((512, 128, 8), True), ((256, 64, 4, 1), True),
+                                          ((128, 32, 8, 1), False)])
 def test_batch_matches_single_calls(H, workload, config, graph):
     sc, grids, _, specs = workload
     jobs, refs = _jobs(H, specs, grids, H.traverse_hdda, slack=5)
