@@ -289,6 +289,69 @@ def run_ours(args):
     ms_ss, _, _, _ = timed(sampler_hdda_skip, max(3, K // 2), 2)
     ms_ds, _, _, _ = timed(sampler_dense_skip, max(3, K // 2), 2)
     ms_r, _, kern_r, _ = timed(render_step, K, 2, profile=True)
+
+    # incremental rebuild: 1 % of the 8^3 blocks change (one voxel each, in partial
+    # blocks, so the leaves are rewritten in place) and again 1 % with a new leaf each
+    # (empty blocks gain a voxel: the structure is rebuilt), against the full rebuild
+    def update_bench(occ, aabbs):
+        L, R = occ.shape[0], occ.shape[1]
+        B = (R + 7) // 8
+        blk = occ[:, : B * 8, : B * 8, : B * 8].reshape(L, B, 8, B, 8, B, 8)
+        cnt = blk.sum(axis=(2, 4, 6)).reshape(-1)
+        rng = np.random.default_rng(77)
+        n_pick = max(1, (L * B ** 3) // 100)
+        out = {"blocks": int(L * B ** 3), "listed": n_pick}
+        for kind, cand in (("in_place", np.flatnonzero((cnt > 1) & (cnt < 511))),
+                           ("structural", np.flatnonzero(cnt == 0))):
+            pick = np.sort(rng.choice(cand, size=min(n_pick, cand.size), replace=False))
+            alt = occ.copy()
+            for b in pick:
+                l, r = divmod(int(b), B ** 3)
+                bx, r = divmod(r, B * B)
+                by, bz = divmod(r, B)
+                v = alt[l, 8 * bx:8 * bx + 8, 8 * by:8 * by + 8, 8 * bz:8 * bz + 8]
+                v[0, 0, 0] ^= 1
+            dense_alt = torch.from_numpy(alt).cuda()
+            dense_cur = torch.from_numpy(occ).cuda()
+            lst = torch.from_numpy(pick.astype(np.int64)).cuda()
+            gu = hdda.build_vdb(dense_cur, aabbs)
+            ust = torch.zeros(1, dtype=torch.int32, device="cuda")
+            srcs = (dense_alt, dense_cur)
+            for j in range(4):
+                gu.update(srcs[j % 2], lst, status=ust)
+            torch.cuda.synchronize()
+            reps = 50
+            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for j in range(reps):
+                gu.update(srcs[j % 2], lst, status=ust)
+            b2.record()
+            b2.synchronize()
+            out[kind + "_ms"] = round(a.elapsed_time(b2) / reps, 4)
+            if int(ust.item()) != 0:
+                raise RuntimeError("grid update raised a device status")
+            a.record()
+            for j in range(reps):
+                gu.rebuild(srcs[j % 2])
+            b2.record()
+            b2.synchronize()
+            out["full_rebuild_ms"] = round(a.elapsed_time(b2) / reps, 4)
+            gu.free()
+            del dense_alt, dense_cur
+        return out
+
+    upd = {"object_grid": update_bench(sc.occ, sc.aabbs)}
+    # a large cascade (2 x 512^3, 256 MiB of voxels): the update reads only the listed blocks
+    big_rng = np.random.default_rng(78)
+    big = np.zeros((2, 512, 512, 512), np.uint8)
+    big.reshape(-1)[big_rng.integers(0, big.size, size=big.size // 500)] = 1
+    for l in range(2):
+        for _ in range(40):
+            a0 = big_rng.integers(0, 448, size=3)
+            b0 = a0 + big_rng.integers(8, 64, size=3)
+            big[l, a0[0]:b0[0], a0[1]:b0[1], a0[2]:b0[2]] = 1
+    upd["2x512_grid"] = update_bench(big, scenes.cascade_boxes(2, 1.0))
+    del big
     clk = clocks.stop()
     if int(status.item()) != 0:
         raise RuntimeError(f"hdda_render raised device status {int(status.item())}")
@@ -448,6 +511,7 @@ def run_ours(args):
             "dense_ms_per_frame": round(ms_ds / max(3, K // 2), 4)},
         "dense_dda_step": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_dense / 1e3), 1),
                            "ms_per_step": round(ms_dense / max(3, K // 2), 4)},
+        "incremental_update": upd,
         "render_only_step": {
             "note": "vdb rebuild + hdda_render: the walk, then runs expanded from the lattice "
                     "table and composited in one kernel; no sample, scan or host read-back",

@@ -184,6 +184,35 @@ int hdda_build_vdb(const uint8_t* dense, int levels, int res, const hdda_aabb* a
  */
 int hdda_grid_rebuild(hdda_grid* grid, const uint8_t* dense, hdda_stream_t stream);
 
+/*
+ * Incremental rebuild: updates a VDB grid to new occupancy when only some
+ * 8^3 blocks may have changed (an occupancy update during training touches
+ * part of the grid; the paper's grid is read-only on the GPU and re-pruned
+ * on the CPU, Sec. 5).  The result is bit for bit the grid a full rebuild
+ * from `dense` gives, provided every block outside the list is unchanged.
+ *   dense        device uint8 [levels][res][res][res], the NEW occupancy
+ *   blocks       device int64 [n_blocks]: indices l * B^3 + (bx * B + by) * B
+ *                + bz of the 8^3 blocks that may have changed (B = ceil(res
+ *                / 8), block (bx, by, bz) holds voxels 8 bx .. 8 bx + 7 on x,
+ *                and so on); duplicates are allowed; NULL = every block
+ *   n_blocks     0..2^26 (ignored when blocks is NULL)
+ *   dev_status   NULL: the call synchronises the stream once and returns
+ *                HDDA_ERR_INVALID_ARG if an index lay outside the grid (such
+ *                entries are skipped).  Otherwise a DEVICE uint32 (4-byte
+ *                aligned) that receives the status bits by atomic OR (bit 4 =
+ *                index outside the grid); no synchronisation.
+ * Work: the listed blocks are re-masked from `dense` and compared with the
+ * masks kept from the last build.  When no block changes between empty,
+ * partial and full, only the changed leaves are rewritten in place;
+ * otherwise the node masks and the leaf pool are rebuilt from the kept block
+ * masks (no dense byte outside the list is read).  Scratch of 16 + n_blocks
+ * bytes comes from the stream-ordered allocator.  A dense grid is simply
+ * repacked.  Like hdda_grid_rebuild, it must not overlap traversals of the
+ * grid queued on other streams.
+ */
+int hdda_grid_update(hdda_grid* grid, const uint8_t* dense, const int64_t* blocks,
+                     int64_t n_blocks, uint32_t* dev_status, hdda_stream_t stream);
+
 /* Fills *out (HOST).  Synchronises the grid's last build stream. */
 int hdda_grid_stats_get(const hdda_grid* grid, hdda_grid_stats* out);
 

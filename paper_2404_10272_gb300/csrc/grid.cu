@@ -136,13 +136,17 @@ __device__ uint32_t cta_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t*
   return r;
 }
 
+// `gate` (null: always) lets an incremental update skip the kernel when no
+// block changed between empty, partial and full; the value is the same for
+// every thread of the launch.
 __global__ void vdb_nodes_kernel(int L, int B, int N, const uint8_t* __restrict__ blk_state,
                                  uint32_t* __restrict__ child, uint32_t* __restrict__ tile,
                                  uint32_t* __restrict__ local_prefix,
                                  uint32_t* __restrict__ node_leaves,
                                  uint32_t* __restrict__ node_tiles,
                                  uint32_t* __restrict__ nstate,
-                                 uint32_t* __restrict__ nsuper) {
+                                 uint32_t* __restrict__ nsuper, const unsigned* __restrict__ gate) {
+  if (gate && *gate == 0u) return;
   __shared__ uint32_t warp_tot[33];
   __shared__ uint32_t s_occ[kNodeWords];  // child | tile
   __shared__ uint32_t s_g16[16];          // occupied 16^3 groups
@@ -218,7 +222,9 @@ constexpr int kMaxNodesTotal = HDDA_MAX_LEVELS * (HDDA_MAX_RES / kNodeVox) *
 __global__ void vdb_finalize_kernel(int64_t nodes, const uint32_t* __restrict__ node_leaves,
                                     const uint32_t* __restrict__ node_tiles,
                                     const uint32_t* __restrict__ local_prefix,
-                                    uint32_t* __restrict__ prefix, int64_t* __restrict__ totals) {
+                                    uint32_t* __restrict__ prefix, int64_t* __restrict__ totals,
+                                    const unsigned* __restrict__ gate) {
+  if (gate && *gate == 0u) return;
   __shared__ uint32_t base[kMaxNodesTotal];
   __shared__ uint32_t warp_tot[33];
   uint32_t carry = 0, tiles = 0;
@@ -242,17 +248,15 @@ __global__ void vdb_finalize_kernel(int64_t nodes, const uint32_t* __restrict__ 
   }
 }
 
-__global__ void vdb_scatter_kernel(int L, int B, int N, const uint8_t* __restrict__ blk_state,
-                                   const uint32_t* __restrict__ blk_masks,
-                                   const uint32_t* __restrict__ child,
-                                   const uint32_t* __restrict__ prefix,
-                                   uint32_t* __restrict__ leaves, uint32_t* __restrict__ lsub) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t blk = t >> 4;
-  const int part = (int)(t & 15);
+// Copies the mask of partial block `blk` into its slot of the compact leaf
+// pool (16 threads, one word each) and writes the leaf's refinement masks.
+__device__ __forceinline__ void scatter_block(int64_t blk, int part, int B, int N,
+                                              const uint32_t* __restrict__ blk_masks,
+                                              const uint32_t* __restrict__ child,
+                                              const uint32_t* __restrict__ prefix,
+                                              uint32_t* __restrict__ leaves,
+                                              uint32_t* __restrict__ lsub) {
   const int64_t B3 = (int64_t)B * B * B;
-  if (blk >= (int64_t)L * B3) return;
-  if (blk_state[blk] != kBlockPartial) return;
   const int l = (int)(blk / B3);
   const int64_t b = blk % B3;
   const int bx = (int)(b / ((int64_t)B * B)), by = (int)((b / B) % B), bz = (int)(b % B);
@@ -283,6 +287,93 @@ __global__ void vdb_scatter_kernel(int L, int B, int N, const uint8_t* __restric
     lsub[(int64_t)leaf * kLeafSubWords + 1] = c2hi;
     lsub[(int64_t)leaf * kLeafSubWords + 2] = c4;
   }
+}
+
+__global__ void vdb_scatter_kernel(int L, int B, int N, const uint8_t* __restrict__ blk_state,
+                                   const uint32_t* __restrict__ blk_masks,
+                                   const uint32_t* __restrict__ child,
+                                   const uint32_t* __restrict__ prefix,
+                                   uint32_t* __restrict__ leaves, uint32_t* __restrict__ lsub,
+                                   const unsigned* __restrict__ gate) {
+  if (gate && *gate == 0u) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t blk = t >> 4;
+  if (blk >= (int64_t)L * B * B * B) return;
+  if (blk_state[blk] != kBlockPartial) return;
+  scatter_block(blk, (int)(t & 15), B, N, blk_masks, child, prefix, leaves, lsub);
+}
+
+// Incremental update, step 1: one warp per listed block (every block when
+// `list` is null).  The block's mask and state are recomputed from the dense
+// bytes; a mask that differs is stored and changed[i] set, and flags[0] is
+// set when the block's state (empty, partial, full) changes, since the node
+// masks and the leaf compaction then change too.  An index outside the grid
+// is skipped and raises kDevBadIndex.
+__global__ void vdb_update_blocks_kernel(const uint8_t* __restrict__ dense, int L, int R, int B,
+                                         const int64_t* __restrict__ list, int64_t count,
+                                         uint32_t* __restrict__ blk_masks,
+                                         uint8_t* __restrict__ blk_state,
+                                         uint8_t* __restrict__ changed, unsigned* __restrict__ flags,
+                                         unsigned* __restrict__ status) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= count) return;  // uniform per warp
+  const int64_t B3 = (int64_t)B * B * B;
+  const int64_t blk = list ? list[i] : i;
+  if (blk < 0 || blk >= (int64_t)L * B3) {
+    if (lane == 0) {
+      changed[i] = 0;
+      atomicOr(status, kDevBadIndex);
+    }
+    return;
+  }
+  const int l = (int)(blk / B3);
+  const int64_t b = blk % B3;
+  const int bx = (int)(b / ((int64_t)B * B)), by = (int)((b / B) % B), bz = (int)(b % B);
+  const uint8_t* lvl = dense + (int64_t)l * R * R * R;
+  uint32_t mine = 0;
+  for (int w = 0; w < 16; ++w) {
+    const int v = w * 32 + lane;
+    const int x = bx * 8 + (v >> 6), y = by * 8 + ((v >> 3) & 7), z = bz * 8 + (v & 7);
+    bool on = false;
+    if (x < R && y < R && z < R) on = lvl[((int64_t)x * R + y) * R + z] != 0;
+    const uint32_t bal = __ballot_sync(kFull, on);
+    if (lane == w) mine = bal;
+  }
+  const uint32_t old = lane < 16 ? blk_masks[blk * kLeafWords + lane] : 0u;
+  const bool diff = __any_sync(kFull, lane < 16 && mine != old);
+  const bool any = __any_sync(kFull, lane < 16 && mine != 0u);
+  const bool all = __all_sync(kFull, lane >= 16 || mine == kFull);
+  const uint8_t st = all ? kBlockFull : (any ? kBlockPartial : kBlockEmpty);
+  if (diff && lane < 16) blk_masks[blk * kLeafWords + lane] = mine;
+  if (lane == 0) {
+    changed[i] = diff ? 1 : 0;
+    if (st != blk_state[blk]) {
+      blk_state[blk] = st;
+      flags[0] = 1u;
+    }
+  }
+}
+
+// Incremental update, last step when no block changed state: the changed
+// partial blocks' leaves are rewritten in place (16 threads per listed
+// block); the tree's structure and every other leaf stay as they are.
+__global__ void vdb_rewrite_leaves_kernel(int B, int N, const int64_t* __restrict__ list,
+                                          int64_t count, const uint8_t* __restrict__ changed,
+                                          const unsigned* __restrict__ flags,
+                                          const uint8_t* __restrict__ blk_state,
+                                          const uint32_t* __restrict__ blk_masks,
+                                          const uint32_t* __restrict__ child,
+                                          const uint32_t* __restrict__ prefix,
+                                          uint32_t* __restrict__ leaves,
+                                          uint32_t* __restrict__ lsub) {
+  if (*flags != 0u) return;  // the structure changed: the full scatter ran instead
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = t >> 4;
+  if (i >= count || !changed[i]) return;
+  const int64_t blk = list ? list[i] : i;
+  if (blk_state[blk] != kBlockPartial) return;
+  scatter_block(blk, (int)(t & 15), B, N, blk_masks, child, prefix, leaves, lsub);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,13 +452,14 @@ int launch_build(hdda_grid* g, const uint8_t* dense, cudaStream_t s) {
     HDDA_CUDA_TRY(cudaGetLastError());
     vdb_nodes_kernel<<<(unsigned)g->nodes_total(), kNodeWords, 0, s>>>(
         g->L, g->B, g->N, g->blk_state, g->child, g->tile, g->local_prefix, g->node_leaves,
-        g->node_tiles, g->nstate, g->nsuper);
+        g->node_tiles, g->nstate, g->nsuper, nullptr);
     HDDA_CUDA_TRY(cudaGetLastError());
     vdb_finalize_kernel<<<1, 1024, 0, s>>>(g->nodes_total(), g->node_leaves, g->node_tiles,
-                                          g->local_prefix, g->prefix, g->totals);
+                                          g->local_prefix, g->prefix, g->totals, nullptr);
     HDDA_CUDA_TRY(cudaGetLastError());
     vdb_scatter_kernel<<<blocks_for(nblk * 16, 256), 256, 0, s>>>(
-        g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves, g->lsub);
+        g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves, g->lsub,
+        nullptr);
     kt.stop();
     HDDA_CUDA_TRY(cudaGetLastError());
   }
@@ -449,6 +541,91 @@ extern "C" int hdda_grid_rebuild(hdda_grid* grid, const uint8_t* dense, hdda_str
   if (!grid) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
   if (!dense) return set_error(HDDA_ERR_INVALID_ARG, "dense is NULL");
   return launch_build(grid, dense, (cudaStream_t)stream);
+}
+
+namespace hdda {
+namespace {
+
+// Pinned host word for the synchronous status read of an update.
+struct UpdateWord {
+  unsigned* p = nullptr;
+  ~UpdateWord() { if (p) cudaFreeHost(p); }
+};
+thread_local UpdateWord t_update_word;
+
+int update_vdb(hdda_grid* g, const uint8_t* dense, const int64_t* blocks, int64_t n_blocks,
+               uint32_t* dev_status, cudaStream_t s) {
+  const int64_t count = blocks ? n_blocks : g->blocks_total();
+  if (count == 0) return HDDA_OK;
+  unsigned* hw = nullptr;
+  if (!dev_status) {
+    if (!t_update_word.p) HDDA_CUDA_TRY(cudaMallocHost(&t_update_word.p, sizeof(unsigned)));
+    hw = t_update_word.p;
+  }
+  // scratch: {flags[0] = structure changed, status}, then changed[count]
+  char* scratch = nullptr;
+  HDDA_CUDA_TRY(cudaMallocAsync(&scratch, 16 + (size_t)count, s));
+  unsigned* flags = reinterpret_cast<unsigned*>(scratch);
+  unsigned* status = dev_status ? dev_status : flags + 1;
+  uint8_t* changed = reinterpret_cast<uint8_t*>(scratch + 16);
+  int st = HDDA_OK;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);
+  if (e != cudaSuccess) st = cuda_error(e, "cudaMemsetAsync");
+  if (st == HDDA_OK) {
+    KernelTimer kt("update_vdb", s);  // the update's five kernels together
+    vdb_update_blocks_kernel<<<blocks_for(count * 32, 256), 256, 0, s>>>(
+        dense, g->L, g->R, g->B, blocks, count, g->blk_masks, g->blk_state, changed, flags,
+        status);
+    vdb_nodes_kernel<<<(unsigned)g->nodes_total(), kNodeWords, 0, s>>>(
+        g->L, g->B, g->N, g->blk_state, g->child, g->tile, g->local_prefix, g->node_leaves,
+        g->node_tiles, g->nstate, g->nsuper, flags);
+    vdb_finalize_kernel<<<1, 1024, 0, s>>>(g->nodes_total(), g->node_leaves, g->node_tiles,
+                                          g->local_prefix, g->prefix, g->totals, flags);
+    vdb_scatter_kernel<<<blocks_for(g->blocks_total() * 16, 256), 256, 0, s>>>(
+        g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves, g->lsub,
+        flags);
+    vdb_rewrite_leaves_kernel<<<blocks_for(count * 16, 256), 256, 0, s>>>(
+        g->B, g->N, blocks, count, changed, flags, g->blk_state, g->blk_masks, g->child,
+        g->prefix, g->leaves, g->lsub);
+    kt.stop();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_error(e, "update kernels");
+  }
+  if (st == HDDA_OK && !dev_status) {
+    e = cudaMemcpyAsync(hw, flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_error(e, "cudaMemcpyAsync(status)");
+  }
+  e = cudaFreeAsync(scratch, s);
+  if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
+  if (st != HDDA_OK) return st;
+  HDDA_CUDA_TRY(cudaEventRecord(g->built, s));
+  if (dev_status) return HDDA_OK;
+  HDDA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (*hw & kDevBadIndex)
+    return set_error(HDDA_ERR_INVALID_ARG, "a block index lies outside the grid (skipped)");
+  return HDDA_OK;
+}
+
+}  // namespace
+}  // namespace hdda
+
+extern "C" int hdda_grid_update(hdda_grid* grid, const uint8_t* dense, const int64_t* blocks,
+                                int64_t n_blocks, uint32_t* dev_status, hdda_stream_t stream) {
+  clear_error();
+  if (!grid) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
+  if (!dense) return set_error(HDDA_ERR_INVALID_ARG, "dense is NULL");
+  if (blocks && (n_blocks < 0 || n_blocks > ((int64_t)1 << 26)))
+    return set_error(HDDA_ERR_INVALID_ARG, "n_blocks=%lld outside 0..2^26", (long long)n_blocks);
+  if (reinterpret_cast<uintptr_t>(dev_status) % 4 != 0)
+    return set_error(HDDA_ERR_INVALID_ARG, "dev_status must be 4-byte aligned");
+  int dev = 0;
+  HDDA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != grid->device)
+    return set_error(HDDA_ERR_INVALID_ARG, "grid lives on device %d, current is %d",
+                     grid->device, dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (grid->kind == HDDA_GRID_DENSE) return launch_build(grid, dense, s);  // one repack
+  return update_vdb(grid, dense, blocks, n_blocks, dev_status, s);
 }
 
 extern "C" int hdda_grid_stats_get(const hdda_grid* g, hdda_grid_stats* out) {

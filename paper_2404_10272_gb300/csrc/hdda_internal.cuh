@@ -41,6 +41,7 @@ enum DeviceStatus : uint32_t {
   kDevInternal = 1u << 1,
   kDevCapacity = 1u << 2,
   kDevTimeout = 1u << 3,
+  kDevBadIndex = 1u << 4,
 };
 
 struct LevelDev {

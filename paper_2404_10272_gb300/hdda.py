@@ -30,7 +30,7 @@ EXPORTED = [
     "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
     "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine", "hdda_batch_create",
     "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free", "hdda_grid_set_walk",
-    "hdda_render",
+    "hdda_render", "hdda_grid_update",
 ]
 
 
@@ -99,6 +99,7 @@ def load(path: str | None = None):
     lib.hdda_build_vdb.argtypes = [vp, i32, i32, ctypes.POINTER(AABB), ctypes.POINTER(vp),
                                    ctypes.POINTER(sz), vp]
     lib.hdda_grid_rebuild.argtypes = [vp, vp, vp]
+    lib.hdda_grid_update.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.hdda_grid_stats_get.argtypes = [vp, ctypes.POINTER(GridStats)]
     lib.hdda_grid_copy_array.argtypes = [vp, i32, vp, sz, ctypes.POINTER(sz)]
     lib.hdda_grid_set_refine.argtypes = [vp, i32]
@@ -202,6 +203,22 @@ class Grid:
     def rebuild(self, dense: torch.Tensor, stream=None):
         d = _cuda(dense, torch.uint8)
         _check(load().hdda_grid_rebuild(self._h, _ptr(d), _stream(stream)))
+
+    def update(self, dense: torch.Tensor, blocks: torch.Tensor | None = None,
+               status: torch.Tensor | None = None, stream=None):
+        """Incremental rebuild (hdda_grid_update): `blocks` is a CUDA int64 tensor of the
+        8^3-block indices l*B^3 + (bx*B + by)*B + bz that may have changed (None: all)."""
+        d = _cuda(dense, torch.uint8)
+        bp, nb = None, 0
+        if blocks is not None:
+            b = _cuda(blocks, torch.int64)
+            bp, nb = _ptr(b), int(b.numel())
+        st = 0
+        if status is not None:
+            if not status.is_cuda or status.numel() < 1 or status.element_size() != 4:
+                raise ValueError("status must be a CUDA tensor of 4-byte elements")
+            st = status.data_ptr()
+        _check(load().hdda_grid_update(self._h, _ptr(d), bp, nb, st, _stream(stream)))
 
     def free(self):
         if self._h:
