@@ -9,18 +9,24 @@ while others are running join them on the GPU instead of waiting for a batch
 boundary.  Each admission point takes every queued request that fits, in
 order (one "tick").
 
-The estimate is rays x (rays, offsets, colours, traversal scratch) plus
-samples x 12 bytes, with samples per ray taken from a per-scene decaying
-maximum over completed requests, plus headroom.  If a frame needs more samples than
-reserved, the sampler reports the exact total and the slot re-runs at that
-size.
+Two executor modes:
+  "samples"  the frame goes through the sample buffers (traversal, then
+             compositing), as the paper's renderer does.  The estimate is rays
+             x (rays, offsets, colours, traversal scratch) plus samples x 12
+             bytes, with samples per ray taken from a per-scene decaying
+             maximum over completed requests, plus headroom.  If a frame needs
+             more samples than reserved, the sampler reports the exact total
+             and the slot re-runs at that size.
+  "render"   the render-only path (hdda_render): no sample buffers, so a
+             request costs a fixed number of bytes per ray, never re-runs, and
+             the library does not wait for the device before the frame's copy.
 
 Per request, in the slot's stream:
   1. the rays are copied to the device;
-  2. the HDDA sampler walks them (walk, scan and emit, one host read of the
-     total);
-  3. the compositor renders the frame;
-  4. the frame is copied back to pinned host memory.
+  2. "samples": the HDDA sampler walks them (walk, scan and emit, one host
+     read of the total) and the compositor renders the frame; "render": the
+     walk and the run-level compositor render it;
+  3. the frame is copied back to pinned host memory.
 
 Latency runs from arrival to the frame in host memory.  The library calls
 release the GIL, so the slots' GPU work overlaps.
@@ -38,6 +44,7 @@ from dataclasses import dataclass, field
 
 BYTES_PER_RAY = 24 + 8 + 16 + 4 + 1 + 128 + 24  # rays, offsets, rgba, counts, runs, slack
 BYTES_PER_SAMPLE = 12
+BYTES_PER_RAY_RENDER = 24 + 16 + 4 + 1 + 128 + 8  # rays, rgba, counts, runs, slack
 
 
 @dataclass
@@ -68,9 +75,12 @@ class Admission:
     """FIFO admission against a device-memory budget and a slot count."""
 
     def __init__(self, budget_bytes: int, slots: int, samples_per_ray_hint: float = 64.0,
-                 headroom: float = 1.5):
+                 headroom: float = 1.5, bytes_per_ray: int = BYTES_PER_RAY,
+                 bytes_per_sample: int = BYTES_PER_SAMPLE):
         self.budget = int(budget_bytes)
         self.slots = int(slots)
+        self.bytes_per_ray = bytes_per_ray
+        self.bytes_per_sample = bytes_per_sample
         self.in_use = 0
         self.busy = 0
         self.headroom = headroom
@@ -79,11 +89,13 @@ class Admission:
         self.queue: collections.deque = collections.deque()
 
     def estimate_samples(self, req: Request) -> int:
+        if not self.bytes_per_sample:
+            return 0
         return int(req.n_rays * self.spr.get(req.scene, self.hint) * self.headroom) + 1024
 
     def estimate_bytes(self, req: Request, samples: int | None = None) -> int:
         s = self.estimate_samples(req) if samples is None else samples
-        return req.n_rays * BYTES_PER_RAY + s * BYTES_PER_SAMPLE
+        return req.n_rays * self.bytes_per_ray + s * self.bytes_per_sample
 
     def push(self, req: Request) -> None:
         self.queue.append(req)
@@ -128,7 +140,10 @@ class RenderServer:
 
     def __init__(self, executor, slots: int, budget_bytes: int, samples_per_ray_hint: float = 64.0):
         self.exec = executor
-        self.adm = Admission(budget_bytes, slots, samples_per_ray_hint)
+        self.adm = Admission(budget_bytes, slots, samples_per_ray_hint,
+                             bytes_per_ray=getattr(executor, "bytes_per_ray", BYTES_PER_RAY),
+                             bytes_per_sample=getattr(executor, "bytes_per_sample",
+                                                      BYTES_PER_SAMPLE))
         self.cv = threading.Condition()
         self.stopping = False
         self.completed: list[Request] = []
@@ -206,11 +221,17 @@ class NeedMore(Exception):
 
 
 class GpuExecutor:
-    """Renders requests on the GPU: resident scenes, one CUDA stream per slot."""
+    """Renders requests on the GPU: resident scenes, one CUDA stream per slot.
+    mode "samples" (sample buffers, then compositing) or "render" (hdda_render)."""
 
-    def __init__(self, scene_list, slots: int):
+    def __init__(self, scene_list, slots: int, mode: str = "samples"):
         import torch
         from . import hdda
+        if mode not in ("samples", "render"):
+            raise ValueError(f"unknown mode {mode!r}")
+        self.mode = mode
+        self.bytes_per_ray = BYTES_PER_RAY if mode == "samples" else BYTES_PER_RAY_RENDER
+        self.bytes_per_sample = BYTES_PER_SAMPLE if mode == "samples" else 0
         self.torch = torch
         self.hdda = hdda
         self.grids, self.fields, self.params = [], [], []
@@ -222,6 +243,7 @@ class GpuExecutor:
                                                 p.max_steps))
         torch.cuda.synchronize()
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.status = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in range(slots)]
 
     def warm(self) -> None:
         """First use of each scene's lattice synchronises; do it before serving."""
@@ -231,6 +253,8 @@ class GpuExecutor:
             hdda.traverse_hdda(o, o + 1.0, g, prm, count_only=True)
 
     def __call__(self, slot: int, req: Request, reserved_bytes: int) -> None:
+        if self.mode == "render":
+            return self._render(slot, req)
         torch, hdda = self.torch, self.hdda
         s = self.streams[slot]
         n = req.n_rays
@@ -251,6 +275,24 @@ class GpuExecutor:
             host.copy_(rgba, non_blocking=True)
             s.synchronize()
         req.samples = smp.total
+        req.rgba = host
+
+    def _render(self, slot: int, req: Request) -> None:
+        torch, hdda = self.torch, self.hdda
+        s = self.streams[slot]
+        n = req.n_rays
+        st = self.status[slot]
+        with torch.cuda.stream(s):
+            o = req.rays_o.to("cuda", non_blocking=True)
+            d = req.rays_d.to("cuda", non_blocking=True)
+            st.zero_()
+            g, prm, fld = self.grids[req.scene], self.params[req.scene], self.fields[req.scene]
+            rgba = hdda.render(o, d, g, prm, fld, status=st, stream=s)
+            host = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
+            host.copy_(rgba, non_blocking=True)
+            s.synchronize()
+        if int(st.item()) != 0:
+            raise RuntimeError(f"hdda_render raised device status {int(st.item())}")
         req.rgba = host
 
 

@@ -59,3 +59,35 @@ def test_alone_equals_mixed_and_direct(setup):
     rgba = hdda.composite(o.cuda(), d.cuda(), s, ex.fields[1]).cpu()
     assert s.total == alone.samples
     assert (rgba - alone.rgba).abs().max().item() <= TOL
+
+
+def test_render_mode_alone_equals_mixed_and_direct(setup):
+    hdda, sc, _ = setup
+    ex = serve.GpuExecutor(sc, slots=4, mode="render")
+    ex.warm()
+    o, d = _rays(2, 320, 240)
+    alone = serve.Request(rid=0, scene=1, rays_o=o, rays_d=d)
+    srv = serve.RenderServer(ex, slots=4, budget_bytes=1 << 30)
+    srv.submit(alone)
+    srv.close()
+    assert alone.error is None and alone.retries == 0
+    srv = serve.RenderServer(ex, slots=4, budget_bytes=1 << 30)
+    mix = []
+    for i in range(12):
+        oo, dd = _rays(200 + i, 64 + 40 * i, 48 + 30 * i)
+        mix.append(serve.Request(rid=i + 1, scene=i % 2, rays_o=oo, rays_d=dd))
+    target = serve.Request(rid=99, scene=1, rays_o=o, rays_d=d)
+    for r in mix[:6] + [target] + mix[6:]:
+        srv.submit(r)
+    srv.close()
+    assert all(r.error is None and r.retries == 0 for r in mix + [target])
+    assert srv.max_concurrent > 1
+    assert torch.equal(target.rgba, alone.rgba)
+    # direct API, and the sample-buffer path within the compositor's tolerance
+    p = sc[1].params
+    prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    direct = hdda.render(o.cuda(), d.cuda(), ex.grids[1], prm, ex.fields[1]).cpu()
+    assert torch.equal(direct, alone.rgba)
+    s = hdda.traverse_hdda(o.cuda(), d.cuda(), ex.grids[1], prm)
+    two = hdda.composite(o.cuda(), d.cuda(), s, ex.fields[1]).cpu()
+    assert (two - alone.rgba).abs().max().item() <= 2 * TOL

@@ -114,3 +114,19 @@ def test_failed_request_does_not_stop_the_server():
         srv.submit(r)
     srv.close()
     assert [r.error is not None for r in reqs] == [False, True, False, False]
+
+
+def test_admission_without_sample_buffers():
+    """Render mode: a request costs bytes per ray only, whatever the scene's history."""
+    adm = serve.Admission(budget_bytes=10_000, slots=8, bytes_per_ray=100, bytes_per_sample=0)
+    reqs = [serve.Request(rid=i, scene=0, rays_o=np.zeros((30, 3)), rays_d=np.zeros((30, 3)))
+            for i in range(5)]
+    for r in reqs:
+        adm.push(r)
+    got = adm.pop_admissible()
+    assert [r.rid for r in got] == [0, 1, 2]          # 3 x 3000 bytes fit in 10000
+    assert all(r.reserved == 3000 for r in got)
+    r = got[0]
+    r.samples = 10 ** 6                               # no effect on later estimates
+    adm.release(r)
+    assert adm.estimate_bytes(reqs[3]) == 3000
