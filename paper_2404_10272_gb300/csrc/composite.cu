@@ -71,9 +71,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
         n0 = __ldg(t0 + p + 32);
         n1 = __ldg(t1 + p + 32);
       }
-      int own = 0;  // the last lane whose first sample is <= p
+      int own = 0;  // the last ray slot whose first sample is <= p
 #pragma unroll
-      for (int s = 16; s > 0; s >>= 1) {
+      for (int s = kRaysPerWarp / 2; s > 0; s >>= 1) {
         const int64_t v = __shfl_sync(kFull, sb, own + s);
         if (v <= p) own += s;
       }

@@ -276,9 +276,18 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
   const int nr = r < n ? (int)nruns[r] : 0;
   uint2* my_runs = s_runs[warp];
   if (capacity > 0) {
+    // four independent loads in flight per lane (the runs of one index j are
+    // contiguous over the warp's lanes)
     const int kept = min(nr, kMaxRuns);
-    for (int j = 0; __any_sync(kFull, j < kept); ++j)
-      if (j < kept) my_runs[j * 32 + lane] = __ldg(runs + (int64_t)j * n + r);
+    for (int j0 = 0; __any_sync(kFull, j0 < kept); j0 += 4) {
+      uint2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u < kept) v[u] = __ldg(runs + (int64_t)(j0 + u) * n + r);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u < kept) my_runs[(j0 + u) * 32 + lane] = v[u];
+    }
     __syncwarp();
   }
   int64_t inc = c;
