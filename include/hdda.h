@@ -138,11 +138,13 @@ typedef enum {
        group g = (gx*8 + gy)*8 + gz with gc = (voxel_c % 128) / 16.  A bit is
        set when the group holds an occupied voxel.                           */
     HDDA_ARRAY_NODE_SUPER = 6,
-    /* uint32 [n_leaves][3] refinement masks of each leaf (VDB), leaf order as
+    /* uint32 [n_leaves][5] refinement masks of each leaf (VDB), leaf order as
        HDDA_ARRAY_LEAVES: words 0-1 = 64 bits, one per 2^3-voxel cell
        c = (cx*4 + cy)*4 + cz with cc = (voxel_c % 8) / 2; word 2 = 8 bits,
        one per 4^3-voxel cell c = (cx*2 + cy)*2 + cz with cc = (voxel_c % 8)
-       / 4.  A bit is set when the cell holds an occupied voxel.             */
+       / 4 (a bit is set when the cell holds an occupied voxel); words 3-4 =
+       64 bits over the 2^3-voxel cells again, set when all 8 voxels of the
+       cell are occupied.                                                     */
     HDDA_ARRAY_LEAF_SUB = 7
 } hdda_array;
 

@@ -261,9 +261,10 @@ def vdb_refinement(v: dict) -> tuple[np.ndarray, np.ndarray]:
     Per node, 18 uint32 words: 64 bits for its 4^3 groups of 32^3 voxels
     (group (gx*4 + gy)*4 + gz), then 512 bits for its 8^3 groups of 16^3
     voxels ((gx*8 + gy)*8 + gz); a bit is set when the group holds a child
-    or a tile.  Per leaf, 3 words: 64 bits for its 4^3 cells of 2^3 voxels
-    ((cx*4 + cy)*4 + cz), then 8 bits for its 2^3 cells of 4^3 voxels; a
-    bit is set when the cell holds an occupied voxel.
+    or a tile.  Per leaf, 5 words: 64 bits for its 4^3 cells of 2^3 voxels
+    ((cx*4 + cy)*4 + cz), then 8 bits for its 2^3 cells of 4^3 voxels, a bit
+    set when the cell holds an occupied voxel; then 64 bits for the 2^3-voxel
+    cells again, a bit set when all 8 voxels of the cell are occupied.
     """
     L, N = v["levels"], v["nodes"]
     occ = (np.unpackbits(v["child"].view(np.uint8), bitorder="little")
@@ -273,13 +274,15 @@ def vdb_refinement(v: dict) -> tuple[np.ndarray, np.ndarray]:
     pack = lambda b: np.packbits(b.reshape(L, N ** 3, -1), axis=-1, bitorder="little").view("<u4")
     nsuper = np.concatenate([pack(g32), pack(g16)], axis=-1)
     leaves = v["leaves"]
-    lsub = np.zeros((leaves.shape[0], 3), np.uint32)
+    lsub = np.zeros((leaves.shape[0], 5), np.uint32)
     if leaves.shape[0]:
         bits = np.unpackbits(leaves.view(np.uint8), bitorder="little").reshape(-1, 8, 8, 8)
         c2 = bits.reshape(-1, 4, 2, 4, 2, 4, 2).any(axis=(2, 4, 6))
         c4 = c2.reshape(-1, 2, 2, 2, 2, 2, 2).any(axis=(2, 4, 6))
+        f2 = bits.reshape(-1, 4, 2, 4, 2, 4, 2).all(axis=(2, 4, 6))
         lsub[:, 0:2] = np.packbits(c2.reshape(-1, 64), axis=-1, bitorder="little").view("<u4")
         lsub[:, 2] = np.packbits(c4.reshape(-1, 8), axis=-1, bitorder="little")[:, 0]
+        lsub[:, 3:5] = np.packbits(f2.reshape(-1, 64), axis=-1, bitorder="little").view("<u4")
     return nsuper.astype(np.uint32), lsub
 
 

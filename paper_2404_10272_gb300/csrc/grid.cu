@@ -249,7 +249,8 @@ __global__ void vdb_finalize_kernel(int64_t nodes, const uint32_t* __restrict__ 
 }
 
 // Copies the mask of partial block `blk` into its slot of the compact leaf
-// pool (16 threads, one word each) and writes the leaf's refinement masks.
+// pool (16 threads, one word each) and writes the leaf's refinement masks
+// (occupied 2^3 and 4^3 cells, fully occupied 2^3 cells).
 __device__ __forceinline__ void scatter_block(int64_t blk, int part, int B, int N,
                                               const uint32_t* __restrict__ blk_masks,
                                               const uint32_t* __restrict__ child,
@@ -269,23 +270,28 @@ __device__ __forceinline__ void scatter_block(int64_t blk, int part, int B, int 
   leaves[(int64_t)leaf * kLeafWords + part] = blk_masks[blk * kLeafWords + part];
   if (part == 0) {
     const uint32_t* m = blk_masks + blk * kLeafWords;
-    uint32_t c2lo = 0, c2hi = 0, c4 = 0;
+    uint32_t c2[2] = {0u, 0u}, f2[2] = {0u, 0u}, c4 = 0;
     for (int cell = 0; cell < 64; ++cell) {  // 2^3 cells, (cx*4 + cy)*4 + cz
       const int cx = cell >> 4, cy = (cell >> 2) & 3, cz = cell & 3;
-      bool any = false;
+      bool any = false, all = true;
       for (int a = 0; a < 8; ++a) {
         const int v = ((2 * cx + (a >> 2)) * 8 + (2 * cy + ((a >> 1) & 1))) * 8 + 2 * cz + (a & 1);
-        any |= (m[v >> 5] >> (v & 31)) & 1u;
+        const bool on = (m[v >> 5] >> (v & 31)) & 1u;
+        any |= on;
+        all &= on;
       }
       if (any) {
-        if (cell < 32) c2lo |= 1u << cell;
-        else c2hi |= 1u << (cell - 32);
+        c2[cell >> 5] |= 1u << (cell & 31);
         c4 |= 1u << (((cx >> 1) * 2 + (cy >> 1)) * 2 + (cz >> 1));
       }
+      if (all) f2[cell >> 5] |= 1u << (cell & 31);
     }
-    lsub[(int64_t)leaf * kLeafSubWords + 0] = c2lo;
-    lsub[(int64_t)leaf * kLeafSubWords + 1] = c2hi;
-    lsub[(int64_t)leaf * kLeafSubWords + 2] = c4;
+    uint32_t* out = lsub + (int64_t)leaf * kLeafSubWords;
+    out[0] = c2[0];
+    out[1] = c2[1];
+    out[2] = c4;
+    out[3] = f2[0];
+    out[4] = f2[1];
   }
 }
 

@@ -24,9 +24,10 @@ constexpr int kLeafWords = 512 / 32;            // 16 words per leaf
 // Refinement masks (set bit = the group holds some occupied voxel):
 //   per node: 64 bits for its 4^3 groups of 32^3 voxels, then 512 bits for
 //   its 8^3 groups of 16^3 voxels;  per leaf: 64 bits for its 4^3 cells of
-//   2^3 voxels, then 8 bits for its 2^3 cells of 4^3 voxels.
+//   2^3 voxels, then 8 bits for its 2^3 cells of 4^3 voxels, then 64 bits
+//   for the 2^3-voxel cells that are fully occupied.
 constexpr int kSuperWords = 2 + 16;
-constexpr int kLeafSubWords = 3;
+constexpr int kLeafSubWords = 5;
 
 // Walk variants: dense bit array, VDB tree, VDB tree with refinement masks.
 enum WalkMode : int { kModeDense = 0, kModeVdb = 1, kModeVdbRefined = 2 };

@@ -11,9 +11,11 @@
 //            axis-aligned set that holds x(t_k) and has one occupancy value
 //            throughout.  For dense DDA the region is the voxel; for HDDA it
 //            is the coarsest uniform node of the tree: an empty or full
-//            16^3-block node, an empty or tiled 8^3 block, or a voxel of a
-//            leaf.  Outside every cascade box the region is a half-space the
-//            ray is leaving towards, or everything when it never comes back.
+//            16^3-block node, an empty 32^3 or 16^3 group (refinement), an
+//            empty or tiled 8^3 block, an empty 4^3 cell, an empty or fully
+//            occupied 2^3 cell (refinement), or a voxel of a leaf.  Outside
+//            every cascade box the region is a half-space the ray is leaving
+//            towards, or everything when it never comes back.
 //   cross    the first later lattice point outside the region.  The ray's
 //            parameter at the region's exit plane gives an estimate through
 //            a bucket index over the lattice; two exact probes confirm it

@@ -234,7 +234,7 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
   // voxel of a leaf
   const uint32_t leaf = ld<kSm>(tb.prefix + ng * kNodeWords + w) + __popc(cw & (bit - 1u));
   if constexpr (kMode == kModeVdbRefined) {
-    // empty 4^3 cell, then empty 2^3 cell of the leaf
+    // empty 4^3 cell, then an empty or fully occupied 2^3 cell of the leaf
     const uint32_t* ls = g.lsub + (int64_t)leaf * kLeafSubWords;
     const int c4 = (((i[0] >> 2) & 1) * 2 + ((i[1] >> 2) & 1)) * 2 + ((i[2] >> 2) & 1);
     if (!((__ldg(ls + 2) >> c4) & 1u)) {
@@ -246,13 +246,15 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
       return false;
     }
     const int c2 = (((i[0] >> 1) & 3) * 4 + ((i[1] >> 1) & 3)) * 4 + ((i[2] >> 1) & 3);
-    if (!((__ldg(ls + (c2 >> 5)) >> (c2 & 31)) & 1u)) {
+    const bool c2_any = (__ldg(ls + (c2 >> 5)) >> (c2 & 31)) & 1u;
+    // an empty 2^3 cell, or a fully occupied one: one region either way
+    if (!c2_any || ((__ldg(ls + 3 + (c2 >> 5)) >> (c2 & 31)) & 1u)) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const int a0 = i[c] & ~1;
         clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + 2, g.R));
       }
-      return false;
+      return c2_any;
     }
   }
   const int v = ((i[0] & 7) * 8 + (i[1] & 7)) * 8 + (i[2] & 7);

@@ -232,9 +232,10 @@ def test_table3_sizes(H):
     st = gv.stats()
     v = oracle.build_vdb(sc.occ)
     assert st.n_leaves == v["n_leaves"] and st.n_tiles == v["n_tiles"]
-    # level table + thresholds + node masks + leaves + refinement masks (node and leaf)
+    # level table + thresholds + node masks + leaves + refinement masks (18 words per
+    # node, 5 per leaf)
     assert st.bytes == (36 + 3 * 129 * 4 + (3 * 128 * 4 + 4) + 64 * v["n_leaves"]
-                        + 18 * 4 + 12 * v["n_leaves"])
+                        + 18 * 4 + 20 * v["n_leaves"])
     gv.set_refine(False)
     assert gv.stats().bytes == 36 + 3 * 129 * 4 + (3 * 128 * 4 + 4) + 64 * v["n_leaves"]
 

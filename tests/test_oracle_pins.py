@@ -330,4 +330,13 @@ def test_vdb_refinement_masks_single_voxel():
     assert ns.shape == (1, 1, 18)
     assert ns[0, 0, 0] == 1 << 1 and ns[0, 0, 1] == 0
     assert ns[0, 0, 2] == 1 << 2 and not ns[0, 0, 3:].any()
-    assert ls.tolist() == [[0, 1, 1 << 4]]
+    assert ls.tolist() == [[0, 1, 1 << 4, 0, 0]]
+    # the whole 2^3 cell (4..5, 8..9, 40..41) occupied: the same cell is also full,
+    # bit 32 of the full-cell words (bit 0 of word 4)
+    occ[0, 4:6, 8:10, 40:42] = 1
+    _, ls = oracle.vdb_refinement(oracle.build_vdb(occ))
+    assert ls.tolist() == [[0, 1, 1 << 4, 0, 1]]
+    # one voxel less: occupied but no longer full
+    occ[0, 4, 8, 40] = 0
+    _, ls = oracle.vdb_refinement(oracle.build_vdb(occ))
+    assert ls.tolist() == [[0, 1, 1 << 4, 0, 0]]
