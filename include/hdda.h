@@ -271,11 +271,13 @@ void hdda_grid_free(hdda_grid* grid);
  *                   intervals in ascending k
  *   capacity        0 = count only: offsets and *total_out are filled and
  *                   nothing else is written.  Otherwise, if capacity < total
- *                   the call returns HDDA_ERR_CAPACITY (with *total_out set)
- *                   and writes no sample at or past index capacity.
+ *                   the call returns HDDA_ERR_CAPACITY (with *total_out set),
+ *                   writes no sample at or past index capacity, and clamps
+ *                   the offsets to capacity (so that they describe exactly
+ *                   the samples written and a consumer stays in bounds).
  *   total_out       HOST int64: number of kept intervals
- * One kernel pass; the call synchronises the stream once at the end to read
- * the total, so every output is complete when it returns.
+ * Kernels in stream order; the call synchronises the stream once at the
+ * end to read the total, so every output is complete when it returns.
  */
 int hdda_traverse_dense(const float* rays_o, const float* rays_d, int64_t n_rays,
                         const hdda_grid* grid, const hdda_params* params, int64_t* offsets,
@@ -293,6 +295,26 @@ int hdda_traverse_hdda(const float* rays_o, const float* rays_d, int64_t n_rays,
                        const hdda_grid* grid, const hdda_params* params, int64_t* offsets,
                        int32_t* ray_idx, float* t0, float* t1, int64_t capacity,
                        int64_t* total_out, hdda_stream_t stream);
+
+/*
+ * Either sampler in stream order: the same outputs as hdda_traverse_hdda (a
+ * VDB grid) or hdda_traverse_dense (a dense grid), without the read-back of
+ * the total and without any synchronisation, so that a consumer such as
+ * hdda_composite can be queued right behind it.
+ *   offsets         as above; the total is offsets[n_rays], on the device
+ *   capacity        as above (0 = count only); a capacity below the total
+ *                   raises bit 2 of *dev_status, writes no sample at or past
+ *                   capacity and clamps the offsets to capacity
+ *   dev_status      DEVICE uint32 (required, 4-byte aligned) that receives
+ *                   status bits by atomic OR: bit 1 = internal region check
+ *                   failed, bit 2 = capacity below the total
+ * The first use of a parameter set synchronises once (the lattice is
+ * computed then).  Scratch comes from the stream-ordered allocator.
+ */
+int hdda_traverse_async(const float* rays_o, const float* rays_d, int64_t n_rays,
+                        const hdda_grid* grid, const hdda_params* params, int64_t* offsets,
+                        int32_t* ray_idx, float* t0, float* t1, int64_t capacity,
+                        uint32_t* dev_status, hdda_stream_t stream);
 
 /*
  * Hierarchical-DDA sampler that allocates nothing, for callers that must not

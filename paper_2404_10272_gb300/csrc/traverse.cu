@@ -235,9 +235,12 @@ __global__ void __launch_bounds__(kBS) onepass_kernel(
   }
   __syncthreads();
   const int64_t off = s_prefix + local;
-  if (r < n) offsets[r] = off;
+  // offsets are clamped to the sample buffer when it is too small (as in the
+  // two-pass emit); the total is reported unclamped
+  const int64_t cap = capacity > 0 ? capacity : INT64_MAX;
+  if (r < n) offsets[r] = min(off, cap);
   if (tile == (int)gridDim.x - 1 && threadIdx.x == kBS - 1) {
-    offsets[n] = off + c;
+    offsets[n] = min(off + c, cap);
     *total_out = off + c;
   }
   if (capacity <= 0) return;
@@ -299,8 +302,16 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
     if (lane >= o) inc += y;
   }
   const int64_t off = __ldg(tile_prefix + tile) + inc - c;
-  if (r < n) offsets[r] = off;
-  if (capacity <= 0) return;
+  if (capacity > 0) {
+    // with too small a buffer the CSR offsets are clamped to it, so that a
+    // consumer of the arrays stays in bounds; the status says what happened
+    if (r < n) offsets[r] = min(off, capacity);
+    if (r == n - 1) offsets[n] = min(off + c, capacity);
+    if (__shfl_sync(kFull, off + c, 31) > capacity && lane == 0) atomicOr(status, kDevCapacity);
+  } else {
+    if (r < n) offsets[r] = off;
+    return;
+  }
   const bool overflow = nr > kMaxRuns;
   if (vec) {
     s_end[warp][lane] = off + c;
@@ -506,10 +517,10 @@ const char* emit_name(int mode) {
 int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
                 const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
                 int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
-                cudaStream_t s) {
+                unsigned* dev_status, cudaStream_t s) {
   const int64_t T = (n + 31) / 32;
   unsigned* walk_counter = reinterpret_cast<unsigned*>(scratch);
-  unsigned* status = walk_counter + 1;
+  unsigned* status = dev_status ? dev_status : walk_counter + 1;
   int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
   char* p = scratch + 256;
   int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
@@ -564,6 +575,7 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
     }
   }
   HDDA_CUDA_TRY(cudaGetLastError());
+  if (dev_status) return HDDA_OK;  // stream-ordered: nothing is read back
   return finish(hw, scratch, capacity, total_out, s);
 }
 
@@ -588,7 +600,37 @@ int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_g
   char* scratch = nullptr;
   HDDA_CUDA_TRY(cudaMallocAsync(&scratch, twopass_scratch_bytes(n), s));
   st = run_twopass(ro, rd, n, grid, lat, offsets, ray_idx, t0, t1, capacity, total_out, scratch,
-                   hw, s);
+                   hw, nullptr, s);
+  cudaError_t e = cudaFreeAsync(scratch, s);
+  if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
+  return st;
+}
+
+// The same two passes in stream order: no read-back and no synchronisation;
+// the total stays in offsets[n] and device status bits go to dev_status.
+int traverse_async(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+                   const hdda_params* params, int64_t* offsets, int32_t* ray_idx, float* t0,
+                   float* t1, int64_t capacity, uint32_t* dev_status, cudaStream_t s) {
+  clear_error();
+  if (!dev_status) return set_error(HDDA_ERR_INVALID_ARG, "dev_status is NULL");
+  if (reinterpret_cast<uintptr_t>(dev_status) % 4 != 0)
+    return set_error(HDDA_ERR_INVALID_ARG, "dev_status must be 4-byte aligned");
+  int64_t unused_total = 0;
+  const bool vdb = grid && grid->kind == HDDA_GRID_VDB;
+  int st = check_args(vdb, ro, rd, n, grid, params, offsets, ray_idx, t0, t1, capacity,
+                      &unused_total);
+  if (st != HDDA_OK) return st;
+  LatticeDev lat;
+  st = get_lattice(*params, s, &lat);
+  if (st != HDDA_OK) return st;
+  if (n == 0) {
+    HDDA_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
+    return HDDA_OK;
+  }
+  char* scratch = nullptr;
+  HDDA_CUDA_TRY(cudaMallocAsync(&scratch, twopass_scratch_bytes(n), s));
+  st = run_twopass(ro, rd, n, grid, lat, offsets, ray_idx, t0, t1, capacity, &unused_total,
+                   scratch, nullptr, dev_status, s);
   cudaError_t e = cudaFreeAsync(scratch, s);
   if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
   return st;
@@ -669,6 +711,14 @@ extern "C" int hdda_traverse_dense(const float* rays_o, const float* rays_d, int
                                    int64_t capacity, int64_t* total_out, hdda_stream_t stream) {
   return hdda::traverse(false, rays_o, rays_d, n_rays, grid, params, offsets, ray_idx, t0, t1,
                         capacity, total_out, (cudaStream_t)stream);
+}
+
+extern "C" int hdda_traverse_async(const float* rays_o, const float* rays_d, int64_t n_rays,
+                                   const hdda_grid* grid, const hdda_params* params,
+                                   int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
+                                   int64_t capacity, uint32_t* dev_status, hdda_stream_t stream) {
+  return hdda::traverse_async(rays_o, rays_d, n_rays, grid, params, offsets, ray_idx, t0, t1,
+                              capacity, dev_status, (cudaStream_t)stream);
 }
 
 extern "C" int hdda_traverse_hdda(const float* rays_o, const float* rays_d, int64_t n_rays,

@@ -30,7 +30,7 @@ EXPORTED = [
     "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
     "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine", "hdda_batch_create",
     "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free", "hdda_grid_set_walk",
-    "hdda_render", "hdda_grid_update",
+    "hdda_render", "hdda_grid_update", "hdda_traverse_async",
 ]
 
 
@@ -118,6 +118,8 @@ def load(path: str | None = None):
     lib.hdda_traverse_hdda_noalloc.argtypes = trav
     lib.hdda_composite.argtypes = [vp, vp, i64, vp, vp, vp, vp, i32, vp, vp]
     lib.hdda_render.argtypes = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, i32, vp, vp, vp]
+    lib.hdda_traverse_async.argtypes = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, vp, vp, vp,
+                                        i64, vp, vp]
     lib.hdda_profiler_enable.argtypes = [i32]
     lib.hdda_profiler_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
     for name in EXPORTED:
@@ -306,6 +308,25 @@ def traverse_dense(rays_o, rays_d, grid: Grid, params: Params, out: Samples | No
     exactly; with `out`, its capacity is used (HddaError ERR_CAPACITY if it
     is too small)."""
     return _traverse("hdda_traverse_dense", rays_o, rays_d, grid, params, out, count_only, stream)
+
+
+def traverse_async(rays_o, rays_d, grid: Grid, params: Params, out: Samples,
+                   status: torch.Tensor, stream=None) -> Samples:
+    """Stream-ordered sampler (hdda_traverse_async): HDDA for a VDB grid, dense DDA for a
+    dense grid.  Nothing is read back; `out.total` is left at -1 and the total is
+    `out.offsets[-1]` on the device.  `status` is a CUDA tensor of one 4-byte element
+    that receives status bits (2 = internal check failed, 4 = capacity below the total)."""
+    ro = _cuda(rays_o, torch.float32, (-1, 3))
+    rd = _cuda(rays_d, torch.float32, (-1, 3))
+    if not status.is_cuda or status.numel() < 1 or status.element_size() != 4:
+        raise ValueError("status must be a CUDA tensor of 4-byte elements")
+    n = int(ro.shape[0])
+    _check(load().hdda_traverse_async(_ptr(ro), _ptr(rd), n, grid.handle, ctypes.byref(params),
+                                      _ptr(out.offsets), _ptr(out.ray_idx), _ptr(out.t0),
+                                      _ptr(out.t1), int(out.t0.numel()), status.data_ptr(),
+                                      _stream(stream)))
+    out.total = -1
+    return out
 
 
 def traverse_hdda(rays_o, rays_d, grid: Grid, params: Params, out: Samples | None = None,
