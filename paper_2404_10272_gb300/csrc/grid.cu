@@ -249,8 +249,9 @@ __global__ void vdb_finalize_kernel(int64_t nodes, const uint32_t* __restrict__ 
 }
 
 // Copies the mask of partial block `blk` into its slot of the compact leaf
-// pool (16 threads, one word each) and writes the leaf's refinement masks
-// (occupied 2^3 and 4^3 cells, fully occupied 2^3 cells).
+// pool and writes the leaf's refinement masks (occupied 2^3 and 4^3 cells,
+// fully occupied 2^3 cells).  Called by the 16 threads of one aligned
+// half-warp, `part` = 0..15, all of them together.
 __device__ __forceinline__ void scatter_block(int64_t blk, int part, int B, int N,
                                               const uint32_t* __restrict__ blk_masks,
                                               const uint32_t* __restrict__ child,
@@ -268,30 +269,44 @@ __device__ __forceinline__ void scatter_block(int64_t blk, int part, int B, int 
   const uint32_t bit = 1u << (cell & 31);
   const uint32_t leaf = prefix[ng * kNodeWords + w] + __popc(child[ng * kNodeWords + w] & (bit - 1u));
   leaves[(int64_t)leaf * kLeafWords + part] = blk_masks[blk * kLeafWords + part];
-  if (part == 0) {
-    const uint32_t* m = blk_masks + blk * kLeafWords;
-    uint32_t c2[2] = {0u, 0u}, f2[2] = {0u, 0u}, c4 = 0;
-    for (int cell = 0; cell < 64; ++cell) {  // 2^3 cells, (cx*4 + cy)*4 + cz
-      const int cx = cell >> 4, cy = (cell >> 2) & 3, cz = cell & 3;
-      bool any = false, all = true;
-      for (int a = 0; a < 8; ++a) {
-        const int v = ((2 * cx + (a >> 2)) * 8 + (2 * cy + ((a >> 1) & 1))) * 8 + 2 * cz + (a & 1);
-        const bool on = (m[v >> 5] >> (v & 31)) & 1u;
-        any |= on;
-        all &= on;
-      }
-      if (any) {
-        c2[cell >> 5] |= 1u << (cell & 31);
-        c4 |= 1u << (((cx >> 1) * 2 + (cy >> 1)) * 2 + (cz >> 1));
-      }
-      if (all) f2[cell >> 5] |= 1u << (cell & 31);
+  // refinement masks: each of the 16 threads classifies 4 of the 64 2^3
+  // cells; OR-reductions over the aligned half-warp join them
+  const unsigned half = 0xFFFFu << (threadIdx.x & 16);
+  const uint32_t* m = blk_masks + blk * kLeafWords;
+  uint32_t c2 = 0, f2 = 0, c4 = 0;  // bits of this thread's word (part >> 3) of c2/f2
+  for (int q = 0; q < 4; ++q) {
+    const int cell = 4 * part + q;  // 2^3 cells, (cx*4 + cy)*4 + cz
+    const int cx = cell >> 4, cy = (cell >> 2) & 3, cz = cell & 3;
+    bool any = false, all = true;
+    for (int a = 0; a < 8; ++a) {
+      const int v = ((2 * cx + (a >> 2)) * 8 + (2 * cy + ((a >> 1) & 1))) * 8 + 2 * cz + (a & 1);
+      const bool on = (__ldg(m + (v >> 5)) >> (v & 31)) & 1u;
+      any |= on;
+      all &= on;
     }
+    if (any) {
+      c2 |= 1u << (cell & 31);
+      c4 |= 1u << (((cx >> 1) * 2 + (cy >> 1)) * 2 + (cz >> 1));
+    }
+    if (all) f2 |= 1u << (cell & 31);
+  }
+  uint32_t c2w[2] = {part < 8 ? c2 : 0u, part < 8 ? 0u : c2};
+  uint32_t f2w[2] = {part < 8 ? f2 : 0u, part < 8 ? 0u : f2};
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    c2w[0] |= __shfl_xor_sync(half, c2w[0], o);
+    c2w[1] |= __shfl_xor_sync(half, c2w[1], o);
+    f2w[0] |= __shfl_xor_sync(half, f2w[0], o);
+    f2w[1] |= __shfl_xor_sync(half, f2w[1], o);
+    c4 |= __shfl_xor_sync(half, c4, o);
+  }
+  if (part == 0) {
     uint32_t* out = lsub + (int64_t)leaf * kLeafSubWords;
-    out[0] = c2[0];
-    out[1] = c2[1];
+    out[0] = c2w[0];
+    out[1] = c2w[1];
     out[2] = c4;
-    out[3] = f2[0];
-    out[4] = f2[1];
+    out[3] = f2w[0];
+    out[4] = f2w[1];
   }
 }
 
