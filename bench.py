@@ -497,6 +497,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, rays[0], args.cpu_stride or stride)
+        cpu["all_cores"] = cpu_baseline_all_cores(sc, rays[0],
+                                                  max(1, (args.cpu_stride or stride) // 4))
+    K_cand = lattice_candidates(sc.params)
 
     line = {
         "metric": "rays/sec and samples/sec, HDDA vs dense-DDA on same GB300 (bit-exact); % HBM roofline",
@@ -510,11 +513,15 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "samples_per_s": round(samples * world / (ms / 1e3), 1),
         "samples_per_step": int(S_avg),
+        "candidates_per_ray": K_cand,
         "hdda_sampler": {"rays_per_s": round(n * K * world / (ms_sh / 1e3), 1),
                          "samples_per_s": round(samp_sh * world / (ms_sh / 1e3), 1),
+                         "candidates_per_s": round(n * K_cand * K * world / (ms_sh / 1e3), 1),
                          "ms_per_frame": round(ms_sh / K, 4)},
         "dense_dda_sampler": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_sd / 1e3), 1),
                               "samples_per_s": round(samp_sd * world / (ms_sd / 1e3), 1),
+                              "candidates_per_s": round(n * K_cand * max(3, K // 2) * world
+                                                        / (ms_sd / 1e3), 1),
                               "ms_per_frame": round(ms_sd / max(3, K // 2), 4)},
         "hdda_plain_vdb_sampler": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_sp / 1e3), 1),
                                    "ms_per_frame": round(ms_sp / max(3, K // 2), 4),
@@ -580,6 +587,60 @@ def cpu_baseline(sc, ray_pair, stride):
             "kind": "oracle",
             "sample": f"every {stride}th ray of camera 0 ({sel.size} rays, {int(off[-1])} samples)",
             "sampler_rays_per_s": round(sel.size / (t1 - t0), 1), "seconds": round(t2 - t0, 2)}
+
+
+def _oracle_chunk(job):
+    """One worker's share of the all-cores CPU baseline (runs in a spawned process)."""
+    import oracle
+    o, d, occ, aabbs, p, field = job
+    if o.shape[0] == 0:
+        return 0.0, 0
+    t0 = time.perf_counter()
+    off, _, a, b = oracle.sample(o, d, occ, aabbs, *p)
+    oracle.composite(o, d, off, a, b, field)
+    return time.perf_counter() - t0, int(off[-1])
+
+
+def cpu_baseline_all_cores(sc, ray_pair, stride):
+    """The same oracle on every host core: the rays dealt round-robin into one share per
+    process (spawned, so no process inherits the CUDA context)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    cores = len(os.sched_getaffinity(0))
+    o, d = ray_pair
+    sel = np.arange(0, o.shape[0], stride)
+    p = sc.params
+    prm = (p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    parts = [sel[i::cores] for i in range(cores)]
+    jobs = [(np.ascontiguousarray(o[s]), np.ascontiguousarray(d[s]), sc.occ, sc.aabbs, prm,
+             sc.field) for s in parts]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, [(j[0][:1], j[1][:1]) + j[2:] for j in jobs])  # warm the workers
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_chunk, jobs)
+        wall = time.perf_counter() - t0
+    return {"value": round(sel.size / wall, 1), "unit": "rays/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"every {stride}th ray of camera 0 ({sel.size} rays, "
+                      f"{sum(r[1] for r in res)} samples), split over {cores} processes",
+            "seconds": round(wall, 2)}
+
+
+def lattice_candidates(p) -> int:
+    """Candidates per ray: the length of the shared lattice, by the binary32 recurrence."""
+    import numpy as np
+    f32 = np.float32
+    t, far = f32(p.near), f32(p.far)
+    step, cone, mx = f32(p.step), f32(p.cone), f32(p.max_step)
+    k = 0
+    while True:
+        tn = f32(t + min(max(f32(t * cone), step), mx))
+        if tn > far:
+            return k
+        k += 1
+        t = tn
 
 
 # ---------------------------------------------------------------------------
