@@ -1,9 +1,12 @@
-// walk.cuh -- device code of the per-ray walk shared by the single-call
-// samplers (traverse.cu) and the batched sampler (batch.cu): the lattice
-// view and its bucket index, ray loading, exact point evaluation, region
-// location on a dense or VDB grid, the region crossing search, the walk
-// itself, and the warp-cooperative expansion of runs into samples.  How the
-// walk works and why it is exact is explained at the top of traverse.cu.
+// walk.cuh -- the per-ray walk shared by the single-call samplers
+// (traverse.cu), the render-only path (render.cu) and the batched sampler
+// (batch.cu): the lattice view and its bucket index, ray loading, exact
+// point evaluation, region location on a dense or VDB grid, the region
+// crossing search, the walk itself (from the start, or resumed after its
+// first runs), the warp-cooperative expansion of runs into samples (4-byte
+// and 16-byte stores), the persistent walk kernel with its staged tables and
+// its launch, and the scan of per-tile sample counts.  How the walk works
+// and why it is exact is explained at the top of traverse.cu.
 #pragma once
 
 #include "grid.cuh"

@@ -140,6 +140,16 @@ def _stream(stream=None) -> int:
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _hold(stream, *tensors):
+    """Tensors read by work queued on `stream` (not the current one) stay allocated until
+    that work is done: the caching allocator is told the stream uses them."""
+    if stream is None:
+        return
+    for t in tensors:
+        if isinstance(t, torch.Tensor) and t.is_cuda:
+            t.record_stream(stream)
+
+
 def _ptr(t: torch.Tensor | None):
     if t is None:
         return None
@@ -204,6 +214,7 @@ class Grid:
 
     def rebuild(self, dense: torch.Tensor, stream=None):
         d = _cuda(dense, torch.uint8)
+        _hold(stream, d)
         _check(load().hdda_grid_rebuild(self._h, _ptr(d), _stream(stream)))
 
     def update(self, dense: torch.Tensor, blocks: torch.Tensor | None = None,
@@ -220,6 +231,7 @@ class Grid:
             if not status.is_cuda or status.numel() < 1 or status.element_size() != 4:
                 raise ValueError("status must be a CUDA tensor of 4-byte elements")
             st = status.data_ptr()
+        _hold(stream, d, b if blocks is not None else None)
         _check(load().hdda_grid_update(self._h, _ptr(d), bp, nb, st, _stream(stream)))
 
     def free(self):
@@ -247,6 +259,7 @@ def _dense_args(dense, aabbs):
 def pack_dense(dense, aabbs, stream=None) -> Grid:
     d, L, R, boxes = _dense_args(dense, aabbs)
     h = ctypes.c_void_p()
+    _hold(stream, d)
     _check(load().hdda_pack_dense(_ptr(d), L, R, boxes, ctypes.byref(h), _stream(stream)))
     return Grid(h, GRID_DENSE, L, R)
 
@@ -254,6 +267,7 @@ def pack_dense(dense, aabbs, stream=None) -> Grid:
 def build_vdb(dense, aabbs, stream=None) -> Grid:
     d, L, R, boxes = _dense_args(dense, aabbs)
     h = ctypes.c_void_p()
+    _hold(stream, d)
     _check(load().hdda_build_vdb(_ptr(d), L, R, boxes, ctypes.byref(h), None, _stream(stream)))
     return Grid(h, GRID_VDB, L, R)
 
@@ -321,6 +335,7 @@ def traverse_async(rays_o, rays_d, grid: Grid, params: Params, out: Samples,
     if not status.is_cuda or status.numel() < 1 or status.element_size() != 4:
         raise ValueError("status must be a CUDA tensor of 4-byte elements")
     n = int(ro.shape[0])
+    _hold(stream, ro, rd, out.offsets, out.ray_idx, out.t0, out.t1, status)
     _check(load().hdda_traverse_async(_ptr(ro), _ptr(rd), n, grid.handle, ctypes.byref(params),
                                       _ptr(out.offsets), _ptr(out.ray_idx), _ptr(out.t0),
                                       _ptr(out.t1), int(out.t0.numel()), status.data_ptr(),
@@ -361,6 +376,7 @@ def composite(rays_o, rays_d, samples: Samples, field, out: torch.Tensor | None 
     n = int(ro.shape[0])
     if out is None:
         out = torch.empty((n, 4), dtype=torch.float32, device=ro.device)
+    _hold(stream, ro, rd, f, samples.offsets, samples.t0, samples.t1, out)
     _check(load().hdda_composite(_ptr(ro), _ptr(rd), n, _ptr(samples.offsets), _ptr(samples.t0),
                                  _ptr(samples.t1), _ptr(f), int(f.shape[0]), _ptr(out),
                                  _stream(stream)))
@@ -385,6 +401,7 @@ def render(rays_o, rays_d, grid: Grid, params: Params, field, out: torch.Tensor 
         if not status.is_cuda or status.numel() < 1 or status.element_size() != 4:
             raise ValueError("status must be a CUDA tensor of 4-byte elements")
         st = status.data_ptr()
+    _hold(stream, ro, rd, f, out, status)
     _check(load().hdda_render(_ptr(ro), _ptr(rd), n, grid.handle, ctypes.byref(params), _ptr(f),
                               int(f.shape[0]), _ptr(out), st, _stream(stream)))
     return out
