@@ -43,10 +43,13 @@ L2_FLUSH_BYTES = 256 << 20
 # does in a separate untimed pass.
 COMPOSITE_FP32_PER_BLOB = 11
 KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
-# DRAM bytes (read + write) per launch from ncu --set full of the object-centric step on
+# DRAM bytes (read + write) per launch from ncu --set full of a workload's step on
 # camera 0 (the capture commands are kept with the profile summaries), for the
-# roofline's "traffic"; an entry must be dropped whenever its kernel changes.
-PROFILED_TRAFFIC = {"composite": 237_450_752, "hdda_emit": 269_876_736, "hdda_walk": 15_884_288}
+# roofline's "traffic"; an entry must be dropped whenever its kernel changes, and a
+# workload without a capture reports none.
+PROFILED_TRAFFIC = {
+    "object": {"composite": 237_450_752, "hdda_emit": 269_876_736, "hdda_walk": 15_884_288},
+}
 
 
 def parse_args():
@@ -460,6 +463,8 @@ def run_ours(args):
             ent["blob_evals_per_sample"] = round(evals_step / max(S_avg, 1), 2)
         per_kernel[name] = ent
 
+    traffic = PROFILED_TRAFFIC.get(args.workload, {})
+
     def roof(name):
         launches, tot_ms = kern[name]
         avg = tot_ms / max(1, launches)
@@ -467,13 +472,13 @@ def run_ours(args):
             ach = alg_inst[name] / (avg / 1e3) / 1e12
             return {"kernel": name, "bound": "alu", "achieved": round(ach, 2),
                     "peak": round(alu_peak, 2), "unit": "Tinst/s (FP32 pipe)",
-                    "frac": round(ach / alu_peak, 4), "traffic": PROFILED_TRAFFIC.get(name),
+                    "frac": round(ach / alu_peak, 4), "traffic": traffic.get(name),
                     "alg_bytes": int(alg_bytes.get(name, 0)),
                     "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock"}
         ach = alg_bytes.get(name, 0) / (avg / 1e3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
                 "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
-                "traffic": PROFILED_TRAFFIC.get(name),
+                "traffic": traffic.get(name),
                 "peak_source": peak_src}
 
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
