@@ -125,14 +125,21 @@ __device__ __forceinline__ void clip_cells(float e[3], const Ray& r, const float
 }
 
 // Classifies x and sets e to the region holding it.  Returns its occupancy.
-// kSm: the tables in tb point into shared memory.
+// kSm: the tables in tb point into shared memory.  `gone` carries, from one
+// call to the next along a ray, the levels whose box the ray has left for
+// good: a point outside a box on an axis whose coordinate does not move
+// back towards it stays outside (each coordinate is monotone in k), so
+// those levels need no test, and no half-space, again.  Only finer levels
+// are recorded (the coarsest is tested once per call anyway; measured
+// faster for single-level grids).
 template <int kMode, bool kSm>
 __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const Ray& r,
-                                       const float x[3], float e[3]) {
+                                       const float x[3], float e[3], unsigned& gone) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) e[c] = r.neg[c] ? -INFINITY : INFINITY;
   int l = -1;
   for (int lv = 0; lv < g.L; ++lv) {
+    if (lv + 1 < g.L && ((gone >> lv) & 1u)) continue;
     const LevelDev& B = g.lv[lv];
     bool inside = true;
 #pragma unroll
@@ -159,7 +166,11 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
         }
       }
     }
-    if (never || best < 0) continue;
+    if (never) {
+      if (lv + 1 < g.L) gone |= 1u << lv;
+      continue;
+    }
+    if (best < 0) continue;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       if (c != best) continue;
@@ -351,15 +362,16 @@ __device__ __forceinline__ int64_t walk(const GridDev& g, const Tabs& tb, const 
   float x[3];
   point_at(r, ld<kSm>(lat.tm), x);
   int k = 0;
+  unsigned gone = 0u;  // cascade levels the ray has left for good
   while (k < K) {
     float e[3];
-    bool occ = locate<kMode, kSm>(g, tb, r, x, e);
+    bool occ = locate<kMode, kSm>(g, tb, r, x, e, gone);
     if (outside(x, e, r)) atomicOr(status, kDevInternal);  // region must hold its point
     int kn = cross<kSm>(r, lat, h, k, e, x);
     if constexpr (kSkip) {
       while (!occ && kn < K) {  // leading empty regions
         k = kn;
-        occ = locate<kMode, kSm>(g, tb, r, x, e);
+        occ = locate<kMode, kSm>(g, tb, r, x, e, gone);
         if (outside(x, e, r)) atomicOr(status, kDevInternal);
         kn = cross<kSm>(r, lat, h, k, e, x);
       }
@@ -417,9 +429,10 @@ __device__ __forceinline__ int walk_from(const GridDev& g, const Tabs& tb, const
   float x[3];
   point_at(r, ld<kSm>(lat.tm + k0), x);
   int k = k0;
+  unsigned gone = 0u;
   while (k < K) {
     float e[3];
-    const bool occ = locate<kMode, kSm>(g, tb, r, x, e);
+    const bool occ = locate<kMode, kSm>(g, tb, r, x, e, gone);
     if (outside(x, e, r)) atomicOr(status, kDevInternal);  // region must hold its point
     const int kn = cross<kSm>(r, lat, h, k, e, x);
     if (occ) {
