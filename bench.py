@@ -47,9 +47,7 @@ KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # camera 0 (the capture commands are kept with the profile summaries), for the
 # roofline's "traffic"; an entry must be dropped whenever its kernel changes, and a
 # workload without a capture reports none.
-PROFILED_TRAFFIC = {
-    "object": {"composite": 237_450_752, "hdda_emit": 269_876_736},
-}
+PROFILED_TRAFFIC = {}
 
 
 def parse_args():

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
     __syncwarp();
     const int64_t wbeg = __shfl_sync(kFull, sb, 0);
     const int64_t wend = __shfl_sync(kFull, se, 31);
+    const int sbr = (int)(sb - wbeg);  // a warp's samples fit in 32 bits (4 rays)
     // the next chunk's interval ends are loaded one chunk ahead, so their
     // DRAM latency overlaps the current chunk's field evaluation
     float n0 = 0.f, n1 = 0.f;
@@ -71,11 +72,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
         n0 = __ldg(t0 + p + 32);
         n1 = __ldg(t1 + p + 32);
       }
+      const int pr = (int)(p - wbeg);
       int own = 0;  // the last ray slot whose first sample is <= p
 #pragma unroll
       for (int s = kRaysPerWarp / 2; s > 0; s >>= 1) {
-        const int64_t v = __shfl_sync(kFull, sb, own + s);
-        if (v <= p) own += s;
+        const int v = __shfl_sync(kFull, sbr, own + s);
+        if (v <= pr) own += s;
       }
       const float ox = __shfl_sync(kFull, o[0], own), oy = __shfl_sync(kFull, o[1], own),
                   oz = __shfl_sync(kFull, o[2], own);

@@ -519,16 +519,20 @@ __device__ __forceinline__ void expand_warp_v4(int64_t off, int64_t c, bool over
   const int64_t wbeg = __shfl_sync(kFull, off, 0);
   const int64_t wend = __shfl_sync(kFull, off + c, 31);
   const unsigned ovf = __ballot_sync(kFull, overflow);
+  // positions relative to the warp's first sample fit in 32 bits (32 rays of
+  // at most 2^24 samples): one shuffle per step of the owner search
+  const int rel = (int)(off - wbeg);
   for (int64_t base = wbeg & ~(int64_t)3; base < wend; base += 128) {
     const int64_t q0 = base + 4 * lane;
     const int64_t qs = max(q0, wbeg);  // first position this warp owns
+    const int qsr = (int)(qs - wbeg);
     int own = 0;  // the last lane whose offset is <= qs
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
-      const int64_t v = __shfl_sync(kFull, off, own + s);
-      if (v <= qs) own += s;
+      const int v = __shfl_sync(kFull, rel, own + s);
+      if (v <= qsr) own += s;
     }
-    const int64_t own_off = __shfl_sync(kFull, off, own);
+    const int64_t own_off = wbeg + __shfl_sync(kFull, rel, own);
     if (qs >= wend || qs >= q0 + 4) continue;
     // the run of `own` that holds qs
     int j = 0;
