@@ -72,39 +72,61 @@ __global__ void lattice_count_kernel(hdda_params p, int64_t* out) {
 
 // Fills t, tm and the bucket index of a lattice block laid out as
 // lattice_block_bytes(max_k): t[max_k+1], tm[max_k], kidx[kKidxMax+2], hdr[4].
-__global__ void lattice_fill_kernel(hdda_params p, int K, int max_k, char* __restrict__ block) {
+// One CTA: thread 0 runs the recurrence (it is sequential by definition) and
+// sizes the buckets; then every thread fills buckets, each by a binary search
+// for the first k with key(tm_k) >= its lower bound (tm is non-decreasing).
+constexpr int kFillThreads = 1024;
+
+__global__ void __launch_bounds__(kFillThreads) lattice_fill_kernel(hdda_params p, int K,
+                                                                     int max_k,
+                                                                     char* __restrict__ block) {
+  __shared__ uint32_t s_hdr[3];
   float* t_out = reinterpret_cast<float*>(block);
   float* tm_out = t_out + max_k + 1;
   int* kidx = reinterpret_cast<int*>(tm_out + max_k);
   uint32_t* hdr = reinterpret_cast<uint32_t*>(kidx + kKidxMax + 2);
-  float t = p.near_t;
-  t_out[0] = t;
-  for (int k = 0; k < K; ++k) {
-    const float tn = lattice_next(t, p);
-    t_out[k + 1] = tn;
-    tm_out[k] = __fmul_rn(__fadd_rn(t, tn), 0.5f);
-    t = tn;
+  if (threadIdx.x == 0) {
+    float t = p.near_t;
+    t_out[0] = t;
+    for (int k = 0; k < K; ++k) {
+      const float tn = lattice_next(t, p);
+      t_out[k + 1] = tn;
+      tm_out[k] = __fmul_rn(__fadd_rn(t, tn), 0.5f);
+      t = tn;
+    }
+    uint32_t key0 = 0, shift = 0;
+    int NB = 0;
+    if (K > 0) {
+      key0 = float_key(tm_out[0]);
+      const uint32_t range = float_key(tm_out[K - 1]) - key0;
+      while ((range >> shift) >= (uint32_t)kKidxMax) ++shift;
+      NB = (int)(range >> shift) + 1;
+    }
+    s_hdr[0] = key0;
+    s_hdr[1] = shift;
+    s_hdr[2] = (uint32_t)NB;
+    hdr[0] = key0;
+    hdr[1] = shift;
+    hdr[2] = (uint32_t)NB;
   }
+  __syncthreads();  // thread 0's table is visible to the block from here on
   if (K == 0) {
-    kidx[0] = kidx[1] = 0;
-    hdr[0] = hdr[1] = hdr[2] = 0;
+    if (threadIdx.x == 0) kidx[0] = kidx[1] = 0;
     return;
   }
-  const uint32_t key0 = float_key(tm_out[0]);
-  const uint32_t range = float_key(tm_out[K - 1]) - key0;
-  uint32_t shift = 0;
-  while ((range >> shift) >= (uint32_t)kKidxMax) ++shift;
-  const int NB = (int)(range >> shift) + 1;
-  int k = 0;
-  for (int b = 0; b <= NB; ++b) {
+  const uint32_t key0 = s_hdr[0], shift = s_hdr[1];
+  const int NB = (int)s_hdr[2];
+  for (int b = threadIdx.x; b <= NB; b += blockDim.x) {
     const uint64_t bound = (uint64_t)key0 + ((uint64_t)b << shift);
-    while (k < K && (uint64_t)float_key(tm_out[k]) < bound) ++k;
-    kidx[b] = k;
+    int lo = 0, hi = K;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((uint64_t)float_key(tm_out[mid]) < bound) lo = mid + 1;
+      else hi = mid;
+    }
+    kidx[b] = lo;
   }
-  kidx[NB + 1] = K;
-  hdr[0] = key0;
-  hdr[1] = shift;
-  hdr[2] = (uint32_t)NB;
+  if (threadIdx.x == 0) kidx[NB + 1] = K;
 }
 
 __device__ __forceinline__ int64_t cta_exclusive_scan64(int64_t v, int64_t* total) {
@@ -418,7 +440,7 @@ int get_lattice(const hdda_params& p, cudaStream_t s, LatticeDev* out) {
                      p.max_steps);
   }
   HDDA_CUDA_TRY(cudaMalloc(&e.block, lattice_block_bytes(e.K)));
-  lattice_fill_kernel<<<1, 1, 0, s>>>(key, e.K, e.K, e.block);
+  lattice_fill_kernel<<<1, kFillThreads, 0, s>>>(key, e.K, e.K, e.block);
   HDDA_CUDA_TRY(cudaGetLastError());
   HDDA_CUDA_TRY(cudaStreamSynchronize(s));  // published to every stream from here on
   g_lattices.push_back(e);
@@ -693,7 +715,7 @@ int traverse_with_scratch(bool vdb, const float* ro, const float* rd, int64_t n,
                      "lattice of %lld candidates exceeds the static scratch maximum of %d",
                      (long long)hw[0], max_k);
   const int K = (int)hw[0];
-  lattice_fill_kernel<<<1, 1, 0, s>>>(key, K, max_k, block);
+  lattice_fill_kernel<<<1, kFillThreads, 0, s>>>(key, K, max_k, block);
   HDDA_CUDA_TRY(cudaGetLastError());
   if (n == 0) {
     HDDA_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
