@@ -22,7 +22,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // Blob evaluations (sample x kept blob), counted only while profiling.
 __device__ unsigned long long g_blob_evals;
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32) composite_kernel(
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n,
     const int64_t* __restrict__ offsets, const float* __restrict__ t0,
     const float* __restrict__ t1, const float* __restrict__ field, int G,
