@@ -866,7 +866,7 @@ def run_serve(args):
         for i in range(16):
             srv.submit(make(i))
         srv.drain()
-        burst = [make(100 + i) for i in range(48)]
+        burst = [make(100 + i) for i in range(96)]
         t0 = time.perf_counter()
         for r in burst:
             srv.submit(r)

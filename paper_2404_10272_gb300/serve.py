@@ -244,6 +244,8 @@ class GpuExecutor:
         torch.cuda.synchronize()
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.status = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in range(slots)]
+        self.status_host = [torch.zeros(1, dtype=torch.int32, pin_memory=True)
+                            for _ in range(slots)]
 
     def warm(self) -> None:
         """First use of each scene's lattice synchronises; do it before serving."""
@@ -290,9 +292,11 @@ class GpuExecutor:
             rgba = hdda.render(o, d, g, prm, fld, status=st, stream=s)
             host = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
             host.copy_(rgba, non_blocking=True)
+            sh = self.status_host[slot]
+            sh.copy_(st, non_blocking=True)   # read with the frame: one wait per request
             s.synchronize()
-        if int(st.item()) != 0:
-            raise RuntimeError(f"hdda_render raised device status {int(st.item())}")
+        if int(sh[0]) != 0:
+            raise RuntimeError(f"hdda_render raised device status {int(sh[0])}")
         req.rgba = host
 
 
