@@ -48,9 +48,8 @@ KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # roofline's "traffic"; an entry must be dropped whenever its kernel changes, and a
 # workload without a capture reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 237_030_400, "hdda_emit": 269_890_048, "hdda_walk": 15_894_272},
-    "unbounded": {"composite": 1_503_789_056, "hdda_emit": 2_182_102_784,
-                  "hdda_walk": 26_475_008},
+    "object": {"composite": 237_030_400, "hdda_walk": 15_894_272},
+    "unbounded": {"composite": 1_503_789_056, "hdda_walk": 26_475_008},
 }
 
 

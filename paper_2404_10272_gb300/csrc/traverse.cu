@@ -337,9 +337,10 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
   const bool overflow = nr > kMaxRuns;
   if (vec) {
     s_end[warp][lane] = off + c;
+    runs_to_positions(my_runs, lane, min(nr, kMaxRuns), off, __shfl_sync(kFull, off, 0));
     __syncwarp();
-    expand_warp_v4<true>(off, c, overflow, my_runs, 32, (int32_t)(tile * 32), s_end[warp], lat.t,
-                         capacity, ray_idx, t0, t1);
+    expand_warp_v4(off, c, overflow, my_runs, (int32_t)(tile * 32), s_end[warp], lat.t, capacity,
+                   ray_idx, t0, t1);
   } else {
     expand_warp<true>(off, c, overflow, my_runs, 32, (int32_t)(tile * 32), lat.t, capacity,
                       ray_idx, t0, t1);

@@ -502,16 +502,36 @@ __device__ __forceinline__ void expand_warp(int64_t off, int64_t c, bool overflo
 
 // The same expansion with 16-byte stores: lane i writes the four samples at
 // positions base + 4 i .. base + 4 i + 3 of each 128-position block (base a
-// multiple of 4), so ray_idx, t0 and t1 must be 16-byte aligned.  A lane
-// locates its first position once (owner lane by binary search, then the
-// run), then steps through runs and rays sequentially; s_end[o] holds the
-// end position of lane o's samples.  Vectors that are partial (the warp's
-// first and last), that reach past capacity, or that touch a ray with more
-// runs than were kept are written element by element (the latter's samples
-// not at all: that ray walks again).
-template <bool kSm>
+// multiple of 4), so ray_idx, t0 and t1 must be 16-byte aligned.  Here the
+// runs hold {first k, first output position relative to the warp's first
+// sample} (see runs_to_positions; unused slots have position INT_MAX), so a
+// lane finds its first position's owner lane and run by two binary searches
+// and then steps through runs and rays; s_end[o] holds the end position of
+// lane o's samples.  Vectors that are partial (the warp's first and last),
+// that reach past capacity, or that touch a ray with more runs than were
+// kept are written element by element (the latter's samples not at all:
+// that ray walks again).
+constexpr uint32_t kNoPosition = 0x7fffffffu;
+
+// Lane-local rewrite of a lane's kept runs [k_begin, k_end) into {k_begin,
+// first position relative to wbeg}; slots from `kept` on get kNoPosition.
+__device__ __forceinline__ void runs_to_positions(uint2* runs0, int lane, int kept, int64_t off,
+                                                  int64_t wbeg) {
+  uint32_t q = (uint32_t)(off - wbeg);
+  for (int j = 0; j < kMaxRuns; ++j) {
+    uint2& e = runs0[j * 32 + lane];
+    if (j < kept) {
+      const uint32_t len = e.y - e.x;
+      e.y = q;
+      q += len;
+    } else {
+      e = make_uint2(0u, kNoPosition);
+    }
+  }
+}
+
 __device__ __forceinline__ void expand_warp_v4(int64_t off, int64_t c, bool overflow,
-                                               const uint2* runs0, int64_t stride, int32_t rid0,
+                                               const uint2* runs0, int32_t rid0,
                                                const int64_t* s_end, const float* __restrict__ t,
                                                int64_t capacity, int32_t* __restrict__ ray_idx,
                                                float* __restrict__ t0, float* __restrict__ t1) {
@@ -532,18 +552,18 @@ __device__ __forceinline__ void expand_warp_v4(int64_t off, int64_t c, bool over
       const int v = __shfl_sync(kFull, rel, own + s);
       if (v <= qsr) own += s;
     }
-    const int64_t own_off = wbeg + __shfl_sync(kFull, rel, own);
     if (qs >= wend || qs >= q0 + 4) continue;
-    // the run of `own` that holds qs
+    // the run of `own` that holds qs, its first k and the next run's start
     int j = 0;
-    int64_t loc = qs - own_off;
-    uint2 run = make_uint2(0u, 0u);
+    int k = 0;
+    uint32_t nxt = kNoPosition;
     if (!((ovf >> own) & 1u)) {
-      run = ld<kSm>(runs0 + own);
-      while (loc >= (int64_t)(run.y - run.x)) {
-        loc -= run.y - run.x;
-        run = ld<kSm>(runs0 + own + (++j) * stride);
-      }
+#pragma unroll
+      for (int s = kMaxRuns / 2; s > 0; s >>= 1)
+        if (runs0[(j + s) * 32 + own].y <= (uint32_t)qsr) j += s;
+      const uint2 e = runs0[j * 32 + own];
+      k = (int)e.x + (qsr - (int)e.y);
+      nxt = j + 1 < kMaxRuns ? runs0[(j + 1) * 32 + own].y : kNoPosition;
     }
     int32_t vr[4];
     float va[4], vb[4];
@@ -554,29 +574,33 @@ __device__ __forceinline__ void expand_warp_v4(int64_t off, int64_t c, bool over
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int64_t q = q0 + i;
+      const uint32_t qr = (uint32_t)(q - wbeg);
       ok[i] = false;
       vr[i] = 0;
       va[i] = vb[i] = 0.f;
       if (q < qs || q >= wend) continue;
-      while (q >= s_end[o]) {  // next ray with samples
-        ++o;
+      if (q >= s_end[o]) {  // next ray with samples
+        do {
+          ++o;
+        } while (q >= s_end[o]);
         j = 0;
-        loc = 0;
-        if (!((ovf >> o) & 1u)) run = ld<kSm>(runs0 + o);
+        if (!((ovf >> o) & 1u)) {
+          k = (int)runs0[o].x;
+          nxt = runs0[32 + o].y;
+        }
+      } else if (qr == nxt) {  // next run of the same ray
+        ++j;
+        k = (int)runs0[j * 32 + o].x;
+        nxt = j + 1 < kMaxRuns ? runs0[(j + 1) * 32 + o].y : kNoPosition;
       }
       if ((ovf >> o) & 1u) continue;
-      const int k = (int)run.x + (int)loc;
       vr[i] = rid0 + o;
       va[i] = k == kprev + 1 ? tprev : __ldg(t + k);
       vb[i] = __ldg(t + k + 1);
       kprev = k;
       tprev = vb[i];
       ok[i] = q < capacity;
-      if (++loc == (int64_t)(run.y - run.x)) {
-        loc = 0;
-        ++j;
-        if (j < kMaxRuns) run = ld<kSm>(runs0 + o + j * stride);
-      }
+      ++k;
     }
     if (ok[0] & ok[1] & ok[2] & ok[3]) {
       *reinterpret_cast<int4*>(ray_idx + q0) = make_int4(vr[0], vr[1], vr[2], vr[3]);
