@@ -283,25 +283,22 @@ __global__ void __launch_bounds__(kBS) onepass_kernel(
 
 constexpr int kEmitWarps = 4;
 
-// Pass 2.  One warp per 32-ray tile, independent of every other warp: its
-// offset is the tile's prefix plus a warp scan; its runs go to shared
-// memory and are expanded into samples.
+// Pass 2 for one 32-ray tile, independent of every other tile: its offset
+// is the tile's prefix plus a warp scan; its runs go to shared memory
+// (my_runs: run j of lane i at [j * 32 + i]; my_end: end position of lane
+// i's samples) and are expanded into samples.
 template <int kMode>
-__global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
-    const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
-    LatticeDev lat, const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
+__device__ __forceinline__ void emit_tile(
+    int64_t tile, uint2* my_runs, int64_t* my_end, const float* __restrict__ ro,
+    const float* __restrict__ rd, int64_t n, const GridDev& g, const LatticeDev& lat,
+    const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
     const uint2* __restrict__ runs, const int64_t* __restrict__ tile_prefix,
     int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
     float* __restrict__ t1, int64_t capacity, bool vec, unsigned* __restrict__ status) {
-  __shared__ uint2 s_runs[kEmitWarps][kMaxRuns * 32];  // run j of lane i at [j * 32 + i]
-  __shared__ int64_t s_end[kEmitWarps][32];            // end position of lane i's samples
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t tile = (int64_t)blockIdx.x * kEmitWarps + warp;
-  if (tile * 32 >= n) return;  // uniform per warp
+  const int lane = threadIdx.x & 31;
   const int64_t r = tile * 32 + lane;
   const int64_t c = r < n ? (int64_t)counts[r] : 0;
   const int nr = r < n ? (int)nruns[r] : 0;
-  uint2* my_runs = s_runs[warp];
   if (capacity > 0) {
     // four independent loads in flight per lane (the runs of one index j are
     // contiguous over the warp's lanes)
@@ -336,10 +333,10 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
   }
   const bool overflow = nr > kMaxRuns;
   if (vec) {
-    s_end[warp][lane] = off + c;
+    my_end[lane] = off + c;
     runs_to_positions(my_runs, lane, min(nr, kMaxRuns), off, __shfl_sync(kFull, off, 0));
     __syncwarp();
-    expand_warp_v4(off, c, overflow, my_runs, (int32_t)(tile * 32), s_end[warp], lat.t, capacity,
+    expand_warp_v4(off, c, overflow, my_runs, (int32_t)(tile * 32), my_end, lat.t, capacity,
                    ray_idx, t0, t1);
   } else {
     expand_warp<true>(off, c, overflow, my_runs, 32, (int32_t)(tile * 32), lat.t, capacity,
@@ -353,6 +350,47 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
     walk<kMode, true, false>(g, global_tabs(g), lat, h, ray, nullptr, 0, unused, (int32_t)r, off,
                              capacity, ray_idx, t0, t1, status);
   }
+}
+
+// Pass 2.  Persistent: each warp takes 32-ray tiles from an atomic counter
+// until none is left, so a warp that finishes early takes more tiles
+// instead of idling until its CTA's slowest tile is done.
+template <int kMode>
+__global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
+    const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
+    LatticeDev lat, const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
+    const uint2* __restrict__ runs, const int64_t* __restrict__ tile_prefix,
+    int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
+    float* __restrict__ t1, int64_t capacity, bool vec, unsigned* __restrict__ tile_counter,
+    unsigned* __restrict__ status) {
+  __shared__ uint2 s_runs[kEmitWarps][kMaxRuns * 32];
+  __shared__ int64_t s_end[kEmitWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned T = (unsigned)((n + 31) / 32);
+  for (;;) {
+    unsigned tile = 0;
+    if (lane == 0) tile = atomicAdd(tile_counter, 1u);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= T) break;
+    emit_tile<kMode>(tile, s_runs[warp], s_end[warp], ro, rd, n, g, lat, counts, nruns, runs,
+                     tile_prefix, offsets, ray_idx, t0, t1, capacity, vec, status);
+    __syncwarp();  // the next tile reuses this warp's shared memory
+  }
+}
+
+// Resident CTAs of the persistent emit: one wave, or fewer for small calls.
+template <int kMode>
+unsigned emit_grid(int64_t T) {
+  int dev = 0, sms = 1, per_sm = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_kernel<kMode>,
+                                                    kEmitWarps * 32, 0) != cudaSuccess ||
+      per_sm <= 0)
+    per_sm = 1;
+  const int64_t want = (T + kEmitWarps - 1) / kEmitWarps;
+  const int64_t full = (int64_t)(sms > 0 ? sms : 1) * per_sm;
+  return (unsigned)(want < full ? want : full);
 }
 
 // ---------------------------------------------------------------------------
@@ -536,7 +574,8 @@ const char* emit_name(int mode) {
 }
 
 // Two-pass launch.  Scratch: [0, 256) header {walk counter u32, status u32,
-// total i64}, then tile sums, tile prefixes, counts, run counts, runs.
+// total i64, emit counter u32}, then tile sums, tile prefixes, counts, run
+// counts, runs.
 int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
                 const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
                 int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
@@ -545,6 +584,7 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   unsigned* walk_counter = reinterpret_cast<unsigned*>(scratch);
   unsigned* status = dev_status ? dev_status : walk_counter + 1;
   int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
+  unsigned* emit_counter = reinterpret_cast<unsigned*>(scratch + 16);
   char* p = scratch + 256;
   int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
   p += a256(8 * (size_t)T);
@@ -576,24 +616,23 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   HDDA_CUDA_TRY(cudaGetLastError());
   {
     KernelTimer kt(emit_name(mode), s);
-    const unsigned nb = (unsigned)((T + kEmitWarps - 1) / kEmitWarps);
     const bool vec = ((reinterpret_cast<uintptr_t>(ray_idx) | reinterpret_cast<uintptr_t>(t0) |
                        reinterpret_cast<uintptr_t>(t1)) & 15) == 0;
     switch (mode) {
       case kModeDense:
-        emit_kernel<kModeDense><<<nb, kEmitWarps * 32, 0, s>>>(
+        emit_kernel<kModeDense><<<emit_grid<kModeDense>(T), kEmitWarps * 32, 0, s>>>(
             ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, vec, status);
+            capacity, vec, emit_counter, status);
         break;
       case kModeVdb:
-        emit_kernel<kModeVdb><<<nb, kEmitWarps * 32, 0, s>>>(
+        emit_kernel<kModeVdb><<<emit_grid<kModeVdb>(T), kEmitWarps * 32, 0, s>>>(
             ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, vec, status);
+            capacity, vec, emit_counter, status);
         break;
       default:
-        emit_kernel<kModeVdbRefined><<<nb, kEmitWarps * 32, 0, s>>>(
+        emit_kernel<kModeVdbRefined><<<emit_grid<kModeVdbRefined>(T), kEmitWarps * 32, 0, s>>>(
             ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, vec, status);
+            capacity, vec, emit_counter, status);
         break;
     }
   }
