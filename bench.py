@@ -48,8 +48,9 @@ KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # roofline's "traffic"; an entry must be dropped whenever its kernel changes, and a
 # workload without a capture reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 237_030_400, "hdda_walk": 15_894_272},
-    "unbounded": {"composite": 1_503_789_056, "hdda_walk": 26_475_008},
+    "object": {"composite": 237_030_400, "hdda_emit": 269_582_080, "hdda_walk": 15_894_272},
+    "unbounded": {"composite": 1_502_058_752, "hdda_emit": 2_182_690_816,
+                  "hdda_walk": 26_471_936},
 }
 
 
@@ -455,6 +456,7 @@ def run_ours(args):
         "composite": 24 * n + 8 * (n + 1) + 8 * S_avg + 16 * n + 32 * G,
     }
     alg_inst = {"composite": evals_step * COMPOSITE_FP32_PER_BLOB}
+    traffic = PROFILED_TRAFFIC.get(args.workload, {})
     per_kernel = {}
     for name, (launches, tot_ms) in kern.items():
         avg = tot_ms / max(1, launches)
@@ -462,12 +464,12 @@ def run_ours(args):
         if name in alg_bytes:
             ent["alg_bytes"] = int(alg_bytes[name])
             ent["gbs"] = round(alg_bytes[name] / (avg / 1e3) / 1e9, 1)
+        if name in traffic:
+            ent["traffic"] = traffic[name]
         if name in alg_inst:
             ent["tinst_s"] = round(alg_inst[name] / (avg / 1e3) / 1e12, 2)
             ent["blob_evals_per_sample"] = round(evals_step / max(S_avg, 1), 2)
         per_kernel[name] = ent
-
-    traffic = PROFILED_TRAFFIC.get(args.workload, {})
 
     def roof(name):
         launches, tot_ms = kern[name]
