@@ -48,9 +48,9 @@ KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # roofline's "traffic"; an entry must be dropped whenever its kernel changes, and a
 # workload without a capture reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 237_030_400, "hdda_emit": 269_582_080, "hdda_walk": 15_894_272},
-    "unbounded": {"composite": 1_502_058_752, "hdda_emit": 2_182_690_816,
-                  "hdda_walk": 26_471_936},
+    "object": {"composite": 237_030_400, "hdda_emit": 269_582_080, "hdda_walk": 15_697_152},
+    "unbounded": {"composite": 1_502_856_960, "hdda_emit": 2_182_746_624,
+                  "hdda_walk": 26_248_448},
 }
 
 

@@ -307,7 +307,8 @@ int hdda_traverse_hdda(const float* rays_o, const float* rays_d, int64_t n_rays,
  *                   capacity and clamps the offsets to capacity
  *   dev_status      DEVICE uint32 (required, 4-byte aligned) that receives
  *                   status bits by atomic OR: bit 1 = internal region check
- *                   failed, bit 2 = capacity below the total
+ *                   failed (only while hdda_set_region_checks is on), bit 2 =
+ *                   capacity below the total
  * The first use of a parameter set synchronises once (the lattice is
  * computed then).  Scratch comes from the stream-ordered allocator.
  */
@@ -438,7 +439,7 @@ int hdda_composite(const float* rays_o, const float* rays_d, int64_t n_rays,
  *   field, n_gauss, rgba_out               as for hdda_composite
  *   dev_status   NULL: the call synchronises the stream once at the end and
  *                returns HDDA_ERR_INTERNAL if a device-side region check
- *                failed.  Otherwise a DEVICE uint32 (4-byte aligned) that
+ *                failed (checks on, see hdda_set_region_checks).  Otherwise a DEVICE uint32 (4-byte aligned) that
  *                receives the device status bits by atomic OR (bit 1 =
  *                region check failed); the call then returns once the work
  *                is enqueued and does not synchronise, except on the first
@@ -477,6 +478,26 @@ typedef struct {
 
 int hdda_profiler_enable(int flags);
 int hdda_profiler_read(hdda_kernel_time* out, int cap, int* n_out);
+
+/*
+ * Device-side region checks, off by default (an assertion, as in a debug
+ * build): while on, every walk tests that each region it crosses holds the
+ * lattice point that was classified to find it (the invariant the exact
+ * crossing search of Sec. 3's walk rests on), and a failure raises the internal
+ * status bit, so that the calls above return HDDA_ERR_INTERNAL or set bit 1
+ * of their device status word.  A correct library never fails the check;
+ * it costs about 5 % of the walk, so production runs leave it off.
+ * The checks run in the walk pass of hdda_traverse_hdda, hdda_traverse_dense,
+ * hdda_traverse_async, hdda_render and the batched sampler; the later
+ * passes that re-walk a ray cross the same regions unchecked, and the
+ * allocation-free entry point does not check.  The setting is process-wide
+ * and is read when work is enqueued: a call (or a batch, at
+ * hdda_batch_create) made after the switch sees it.
+ * hdda_set_region_checks returns HDDA_OK; hdda_region_checks returns the
+ * current setting (0 or 1).
+ */
+int hdda_set_region_checks(int on);
+int hdda_region_checks(void);
 
 #ifdef __cplusplus
 }

@@ -62,7 +62,7 @@ __device__ __forceinline__ void warp_copy_grid(GridDev* dst, const GridDev* src)
   __syncwarp();
 }
 
-template <int kMode, int kBlock, bool kSkip>
+template <int kMode, int kBlock, bool kSkip, bool kCheck>
 __global__ void __launch_bounds__(kBlock) batch_walk_kernel(
     const JobDev* __restrict__ jobs, const int64_t* __restrict__ tile0, int J, int64_t T,
     int tiles_per_fetch, int32_t* __restrict__ counts, uint8_t* __restrict__ nruns_out,
@@ -103,8 +103,9 @@ __global__ void __launch_bounds__(kBlock) batch_walk_kernel(
         Ray ray;
         int nr = 0;
         if (load_ray(ro, rd, lr, ray))
-          c = walk<kMode, false, false, kSkip>(g, global_tabs(g), lat, h, ray, runs + gr, slots,
-                                               nr, 0, 0, 0, nullptr, nullptr, nullptr, status);
+          c = walk<kMode, false, false, kSkip, kCheck>(g, global_tabs(g), lat, h, ray, runs + gr,
+                                                       slots, nr, 0, 0, 0, nullptr, nullptr,
+                                                       nullptr, status);
         counts[gr] = (int32_t)c;
         nruns_out[gr] = (uint8_t)min(nr, 255);
       }
@@ -187,6 +188,7 @@ struct hdda_batch {
   int mode = 0;
   int device = 0;
   int64_t T = 0;
+  bool check = false;  // region checks, as set when the batch was created
   hdda_batch_config cfg{};
   hdda::JobDev* jobs = nullptr;  // device
   int64_t* tile0 = nullptr;      // device [J + 1]
@@ -218,7 +220,7 @@ int batch_walk_grid(unsigned* out) {
   HDDA_CUDA_TRY(cudaGetDevice(&dev));
   HDDA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HDDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, batch_walk_kernel<kMode, kBlock, kSkip>, kBlock, 0));
+      &per_sm, batch_walk_kernel<kMode, kBlock, kSkip, false>, kBlock, 0));
   *out = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
   return HDDA_OK;
 }
@@ -237,20 +239,26 @@ int walk_grid_for_block(int block, bool skip, unsigned* out) {
   return skip ? walk_grid_for<kMode, true>(block, out) : walk_grid_for<kMode, false>(block, out);
 }
 
-template <int kMode, bool kSkip>
-void launch_batch_walk_v(const hdda_batch* b, cudaStream_t s) {
+template <int kMode, bool kSkip, bool kCheck>
+void launch_batch_walk_c(const hdda_batch* b, cudaStream_t s) {
   const unsigned grid = b->walk_grid;
   const int tpf = b->cfg.rays_per_fetch / 32;
-#define HDDA_BATCH_WALK(BS)                                                                     \
-  batch_walk_kernel<kMode, BS, kSkip><<<grid, BS, 0, s>>>(b->jobs, b->tile0, b->n_jobs, b->T,  \
-                                                          tpf, b->counts, b->nruns, b->runs,    \
-                                                          b->tile_sum, b->counter, b->status)
+#define HDDA_BATCH_WALK(BS)                                                              \
+  batch_walk_kernel<kMode, BS, kSkip, kCheck><<<grid, BS, 0, s>>>(                       \
+      b->jobs, b->tile0, b->n_jobs, b->T, tpf, b->counts, b->nruns, b->runs, b->tile_sum, \
+      b->counter, b->status)
   switch (b->cfg.walk_block) {
     case 128: HDDA_BATCH_WALK(128); break;
     case 256: HDDA_BATCH_WALK(256); break;
     default: HDDA_BATCH_WALK(512); break;
   }
 #undef HDDA_BATCH_WALK
+}
+
+template <int kMode, bool kSkip>
+void launch_batch_walk_v(const hdda_batch* b, cudaStream_t s) {
+  if (b->check) launch_batch_walk_c<kMode, kSkip, true>(b, s);
+  else launch_batch_walk_c<kMode, kSkip, false>(b, s);
 }
 
 template <int kMode>
@@ -376,6 +384,7 @@ int create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg, hdda_
   b->mode = mode;
   b->device = dev;
   b->T = T;
+  b->check = region_checks_on();
   b->cfg = c;
   b->zero_offsets = zero_offsets;
   const int64_t slots = T * 32;

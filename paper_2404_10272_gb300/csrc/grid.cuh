@@ -53,6 +53,7 @@ struct hdda_grid {
     g.thr = thr; g.bits = bits; g.child = child; g.tile = tile;
     g.prefix = prefix; g.nstate = nstate; g.leaves = leaves;
     g.nsuper = nsuper; g.lsub = lsub;
+    g.check = hdda::region_checks_on() ? 1 : 0;
     return g;
   }
 };

@@ -67,6 +67,7 @@ struct GridDev {
   const uint32_t* leaves;    // vdb: [n_leaves][16]
   const uint32_t* nsuper;    // vdb: [L*N^3][kSuperWords]
   const uint32_t* lsub;      // vdb: [n_leaves][kLeafSubWords]
+  int check;                 // walk checks that each region holds its point
 };
 
 // Buckets of the lattice's inverse index (t -> k), over binary32 keys.
@@ -120,6 +121,8 @@ void clear_error();
 bool profiler_on();
 // True while the work counters are enabled (runtime.cu).
 bool counters_on();
+// True while the walk's device-side region checks are enabled (runtime.cu).
+bool region_checks_on();
 // Blob evaluations counted by the compositor since the last call (composite.cu).
 unsigned long long composite_take_blob_evals();
 // The same count for the render-only path (render.cu).

@@ -36,8 +36,7 @@ template <int kMode>
 __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, const uint8_t* __restrict__ nruns, const uint2* __restrict__ runs,
-    const float* __restrict__ field, int G, float* __restrict__ rgba,
-    unsigned* __restrict__ status, bool count_evals) {
+    const float* __restrict__ field, int G, float* __restrict__ rgba, bool count_evals) {
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kRenderWarps)
   __shared__ float s_T[kRenderWarps][32];
   __shared__ float4 s_C[kRenderWarps][32];
@@ -128,7 +127,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     nr = 0;
     if (more)
       k_next = walk_from<kMode, false>(g, global_tabs(g), lat, h, ray, k_next, sr + lane,
-                                       kRenderRays, nr, status);
+                                       kRenderRays, nr);
     __syncwarp();
   }
   if (has_ray) {
@@ -195,15 +194,15 @@ int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* 
     switch (mode) {
       case kModeDense:
         render_kernel<kModeDense><<<nb, kRenderWarps * 32, fsm, s>>>(
-            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev);
         break;
       case kModeVdb:
         render_kernel<kModeVdb><<<nb, kRenderWarps * 32, fsm, s>>>(
-            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev);
         break;
       default:
         render_kernel<kModeVdbRefined><<<nb, kRenderWarps * 32, fsm, s>>>(
-            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, status, ev);
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev);
         break;
     }
   }

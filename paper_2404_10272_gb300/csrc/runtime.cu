@@ -1,4 +1,5 @@
 // runtime.cu -- error reporting, version and the kernel profiler of the C ABI.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -63,6 +64,12 @@ bool counters_on() {
   return g_count_on;
 }
 
+namespace {
+std::atomic<int> g_region_checks{0};
+}  // namespace
+
+bool region_checks_on() { return g_region_checks.load(std::memory_order_relaxed) != 0; }
+
 KernelTimer::KernelTimer(const char* name, cudaStream_t s, bool allow) : name_(name), s_(s) {
   if (!allow) return;
   std::lock_guard<std::mutex> lock(g_prof_mu);
@@ -96,6 +103,13 @@ extern "C" int hdda_profiler_enable(int flags) {
   hdda::g_count_on = (flags & HDDA_PROFILE_COUNTERS) != 0;
   return HDDA_OK;
 }
+
+extern "C" int hdda_set_region_checks(int on) {
+  hdda::g_region_checks.store(on != 0, std::memory_order_relaxed);
+  return HDDA_OK;
+}
+
+extern "C" int hdda_region_checks(void) { return hdda::region_checks_on() ? 1 : 0; }
 
 extern "C" int hdda_profiler_read(hdda_kernel_time* out, int cap, int* n_out) {
   using namespace hdda;

@@ -30,7 +30,8 @@ EXPORTED = [
     "hdda_traverse_hdda", "hdda_composite", "hdda_profiler_enable", "hdda_profiler_read",
     "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine", "hdda_batch_create",
     "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free", "hdda_grid_set_walk",
-    "hdda_render", "hdda_grid_update", "hdda_traverse_async",
+    "hdda_render", "hdda_grid_update", "hdda_traverse_async", "hdda_set_region_checks",
+    "hdda_region_checks",
 ]
 
 
@@ -416,6 +417,18 @@ def profiler_enable(on: bool = True, counters: bool = False):
     (extra device work: time with the timers alone)."""
     flags = (PROFILE_TIMERS if on else 0) | (PROFILE_COUNTERS if counters else 0)
     _check(load().hdda_profiler_enable(flags))
+
+
+def set_region_checks(on: bool = True):
+    """Device-side region checks on or off (process-wide, off by default):
+    while on, a walk that finds a region not holding its point raises
+    HDDA_ERR_INTERNAL (or bit 1 of a device status word)."""
+    _check(load().hdda_set_region_checks(1 if on else 0))
+
+
+def region_checks() -> bool:
+    """The current region-check setting."""
+    return bool(load().hdda_region_checks())
 
 
 def profiler_read() -> dict:

@@ -51,3 +51,20 @@ def test_binding_names_match_header():
     from paper_2404_10272_gb300 import hdda
     assert sorted(hdda.EXPORTED) == declared_functions()
 
+
+
+def test_region_check_switch_is_host_only(libpath):
+    """The region-check switch is a host-side setting (no CUDA call): off by
+    default in a fresh process, read back as set."""
+    import sys
+    code = ("import ctypes, sys; lib = ctypes.CDLL(sys.argv[1]); "
+            "print(lib.hdda_region_checks())")
+    out = subprocess.run([sys.executable, "-c", code, libpath], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "0", out.stderr
+    lib = ctypes.CDLL(libpath)
+    before = lib.hdda_region_checks()
+    try:
+        assert lib.hdda_set_region_checks(1) == 0 and lib.hdda_region_checks() == 1
+        assert lib.hdda_set_region_checks(0) == 0 and lib.hdda_region_checks() == 0
+    finally:
+        lib.hdda_set_region_checks(before)

@@ -155,6 +155,14 @@ def _full_vs_subset(H, sc, o, d, stride, what):
     gv.set_refine(False)
     assert_same(gpu_samples(H, "hdda", ot, dt, gv, prm), vdb, what + " full frame: plain vs refined")
     gv.set_refine(True)
+    # the library default (region checks off), as the benchmark runs it
+    H.set_region_checks(False)
+    try:
+        assert_same(gpu_samples(H, "hdda", ot, dt, gv, prm), vdb, what + " full frame: checks off")
+        assert_same(gpu_samples(H, "dense", ot, dt, gd, prm), dense,
+                    what + " full frame: dense, checks off")
+    finally:
+        H.set_region_checks(True)
     # oracle on a stratified subset of the same launch's rays
     so, sd, sel = subset_rays(o, d, stride, offset=stride // 3)
     ref = oracle_samples(so, sd, sc.occ, sc.aabbs, sc.params)
