@@ -397,36 +397,73 @@ def run_ours(args):
     value = replicas.aggregate_rate(n * K, ms, world)
 
     # --- end to end through the public API with host buffers ---------------
+    # Every step uploads its rays from pinned host memory and reads its frame
+    # back.  As a streaming renderer would, the uploads run on one copy stream
+    # and the read-backs on another, two slots deep, so that step j+1's rays
+    # travel while step j computes and step j's frame returns while step j+1
+    # computes; events keep each slot's buffers from being reused early.
     e2e = None
     if world >= 1:
-        o_host = [torch.from_numpy(o).pin_memory() for o, _ in rays[:4]]
-        d_host = [torch.from_numpy(d).pin_memory() for _, d in rays[:4]]
-        out_host = torch.empty((n, 4), dtype=torch.float32).pin_memory()
-        o_dev = torch.empty_like(O[0])
-        d_dev = torch.empty_like(D[0])
-        steps_e2e = max(3, K // 2)
+        o_host = [torch.from_numpy(o).pin_memory() for o, _ in rays]
+        d_host = [torch.from_numpy(d).pin_memory() for _, d in rays]
+        out_host = [torch.empty((n, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
+        o_dev = [torch.empty_like(O[0]) for _ in range(2)]
+        d_dev = [torch.empty_like(D[0]) for _ in range(2)]
+        frame = [torch.empty_like(rgba) for _ in range(2)]
+        main = torch.cuda.current_stream()
+        h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]    # slot's rays uploaded
+        ev_used = [torch.cuda.Event() for _ in range(2)]  # slot's step computed
+        ev_out = [torch.cuda.Event() for _ in range(2)]   # slot's frame read back
+        steps_e2e = K  # the same camera mix as the timed steps
 
-        def e2e_step(j):
-            c = j % 4
-            o_dev.copy_(o_host[c], non_blocking=True)
-            d_dev.copy_(d_host[c], non_blocking=True)
+        def upload(j):
+            sl, c = j % 2, cam_of(j)
+            h2d.wait_event(ev_used[sl])  # step j-2 is done with this slot's rays
+            with torch.cuda.stream(h2d):
+                o_dev[sl].copy_(o_host[c], non_blocking=True)
+                d_dev[sl].copy_(d_host[c], non_blocking=True)
+            ev_in[sl].record(h2d)
+
+        def compute(j):
+            sl = j % 2
+            main.wait_event(ev_in[sl])
+            main.wait_event(ev_out[sl])  # step j-2's frame has left this slot
             gv.rebuild(dense)
-            hdda.traverse_async(o_dev, d_dev, gv, prm, bufs, tstatus)
-            hdda.composite(o_dev, d_dev, bufs, field, out=rgba)
-            out_host.copy_(rgba, non_blocking=True)
-            return totals[c]
+            hdda.traverse_async(o_dev[sl], d_dev[sl], gv, prm, bufs, tstatus)
+            hdda.composite(o_dev[sl], d_dev[sl], bufs, field, out=frame[sl])
+            ev_used[sl].record(main)
+            d2h.wait_event(ev_used[sl])
+            with torch.cuda.stream(d2h):
+                out_host[sl].copy_(frame[sl], non_blocking=True)
+            ev_out[sl].record(d2h)
 
-        for j in range(2):
-            e2e_step(j)
-        torch.cuda.synchronize()
+        def run_e2e(steps):
+            upload(0)
+            for j in range(steps):
+                if j + 1 < steps:
+                    upload(j + 1)
+                compute(j)
+            torch.cuda.synchronize()
+
+        run_e2e(3)
         t0 = time.perf_counter()
-        for j in range(steps_e2e):
-            e2e_step(j)
-        torch.cuda.synchronize()
+        run_e2e(steps_e2e)
         el = time.perf_counter() - t0
+        # the last frame read back equals the same step run plainly (stream order check)
+        last = steps_e2e - 1
+        gv.rebuild(dense)
+        hdda.traverse_async(O[cam_of(last)], D[cam_of(last)], gv, prm, bufs, tstatus)
+        want = hdda.composite(O[cam_of(last)], D[cam_of(last)], bufs, field).cpu()
+        if int(tstatus.item()) != 0 or not torch.equal(out_host[last % 2], want):
+            raise RuntimeError("pipelined end-to-end frame differs from the plain step")
         e2e = {"value": n * steps_e2e * world / el, "unit": "rays/s",
                "h2d_bytes_per_step": int(2 * n * 3 * 4),
-               "d2h_bytes_per_step": int(n * 4 * 4 + 16)}
+               "d2h_bytes_per_step": int(n * 4 * 4),
+               "overlap": "uploads and read-backs on two copy streams, two slots deep",
+               "cameras": "the same 20-camera cycle as the timed steps",
+               "l2": "not flushed between steps: each step writes and reads its samples "
+                     "(hundreds of MB, more than the L2)"}
 
     # --- roofline of the dominant kernel -----------------------------------
     peaks = {}
