@@ -83,3 +83,50 @@ def test_composite_no_blobs(H):
     s.t1.copy_(torch.tensor([1.0, 2.0]))
     rgba = H.composite(o, d, s, torch.zeros((0, 8), dtype=torch.float32, device="cuda"))
     assert float(rgba.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("which", ["object", "unbounded"])
+def test_benchmark_step_full_size(H, which):
+    """The step the benchmark times, at full size: grid rebuild, stream-ordered
+    sampling into a preallocated buffer, compositing.  Its samples equal the
+    synchronous sampler's bit for bit, and sampled pixels the binary64
+    oracle's within 1e-5."""
+    if which == "object":
+        sc = scenes.object_scene()
+        o, d = scenes.object_cameras(n=1)[0].rays()
+        stride = 211
+    else:
+        sc = scenes.unbounded_scene()
+        o, d = scenes.unbounded_camera().rays()
+        stride = 1009
+    p = sc.params
+    prm = H.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    dense = torch.from_numpy(sc.occ).cuda()
+    field = torch.from_numpy(sc.field).cuda()
+    g = H.build_vdb(dense, sc.aabbs)
+    sync = H.traverse_hdda(ot, dt, g, prm)
+    ref = tuple(to_np(x) for x in sync.trimmed())
+    bufs = H.alloc_samples(ot.shape[0], sync.total)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g.rebuild(dense)
+    H.traverse_async(ot, dt, g, prm, bufs, st)
+    rgba = H.composite(ot, dt, bufs, field)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    off = to_np(bufs.offsets)
+    total = int(off[-1])
+    assert total == sync.total
+    t0 = to_np(bufs.t0[:total])
+    t1 = to_np(bufs.t1[:total])
+    np.testing.assert_array_equal(off, ref[0])
+    np.testing.assert_array_equal(to_np(bufs.ray_idx[:total]), ref[1])
+    np.testing.assert_array_equal(t0.view(np.uint32), ref[2].view(np.uint32))
+    np.testing.assert_array_equal(t1.view(np.uint32), ref[3].view(np.uint32))
+    sel = np.arange(stride // 3, o.shape[0], stride)
+    sub_off = np.concatenate([[0], np.cumsum(off[sel + 1] - off[sel])])
+    idx = np.concatenate([np.arange(off[r], off[r + 1]) for r in sel])
+    want = oracle.composite(o[sel], d[sel], sub_off, t0[idx], t1[idx], sc.field)
+    err = np.abs(to_np(rgba)[sel].astype(np.float64) - want)
+    assert err.max() <= TOL, err.max()
+    assert want[:, 3].max() > 0.5
