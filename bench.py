@@ -43,6 +43,14 @@ L2_FLUSH_BYTES = 256 << 20
 # does in a separate untimed pass.
 COMPOSITE_FP32_PER_BLOB = 11
 KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
+# L2 hit rate and warp execution efficiency (active lanes per warp instruction) per kernel
+# from the same ncu --set full captures (object frame, camera 0); dropped like the traffic
+# when a kernel changes.
+PROFILED_COUNTERS = {
+    "object": {"hdda_walk": {"l2_hit_pct": 37.8, "active_lanes_of_32": 24.61},
+               "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98},
+               "composite": {"l2_hit_pct": 36.5, "active_lanes_of_32": 31.92}},
+}
 # DRAM bytes (read + write) per launch from ncu --set full of a workload's step on
 # camera 0 (the capture commands are kept with the profile summaries), for the
 # roofline's "traffic"; an entry must be dropped whenever its kernel changes, and a
@@ -503,6 +511,7 @@ def run_ours(args):
             ent["gbs"] = round(alg_bytes[name] / (avg / 1e3) / 1e9, 1)
         if name in traffic:
             ent["traffic"] = traffic[name]
+        ent.update(PROFILED_COUNTERS.get(args.workload, {}).get(name, {}))
         if name in alg_inst:
             ent["tinst_s"] = round(alg_inst[name] / (avg / 1e3) / 1e12, 2)
             ent["blob_evals_per_sample"] = round(evals_step / max(S_avg, 1), 2)
@@ -548,6 +557,8 @@ def run_ours(args):
         cpu["all_cores"] = cpu_baseline_all_cores(sc, rays[0],
                                                   max(1, (args.cpu_stride or stride) // 4))
     K_cand = lattice_candidates(sc.params)
+    # t update (2 ops, 5 with a growing step) + midpoint 2 + position 6 + floors 3 + compares 3
+    cand_ops = (5 if sc.params.cone > 0 else 2) + 2 + 6 + 3 + 3
 
     line = {
         "metric": "rays/sec and samples/sec, HDDA vs dense-DDA on same GB300 (bit-exact); % HBM roofline",
@@ -562,6 +573,13 @@ def run_ours(args):
         "samples_per_s": round(samples * world / (ms / 1e3), 1),
         "samples_per_step": int(S_avg),
         "candidates_per_ray": K_cand,
+        "candidate_alu_bound": {
+            "fp32_ops_per_candidate": cand_ops,
+            "ms_per_frame_at_peak": round(n * K_cand * cand_ops / (alu_peak * 1e12) * 1e3, 4),
+            "note": "FP32 issue alone of stepping every lattice candidate (t update, midpoint, "
+                    "position, 3 floors, 3 compares) at the derived FP32 peak; both walks "
+                    "cross regions instead and touch a candidate only to confirm a crossing "
+                    "or to write a kept sample"},
         "hdda_sampler": {"rays_per_s": round(n * K * world / (ms_sh / 1e3), 1),
                          "samples_per_s": round(samp_sh * world / (ms_sh / 1e3), 1),
                          "candidates_per_s": round(n * K_cand * K * world / (ms_sh / 1e3), 1),
