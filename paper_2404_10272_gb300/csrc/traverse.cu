@@ -562,10 +562,12 @@ int run_onepass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+constexpr size_t kTwopassHead = 256;
+
 // Bytes of the two-pass scratch for n rays.
 size_t twopass_scratch_bytes(int64_t n) {
   const int64_t T = (n + 31) / 32;
-  return 256 + 2 * a256(8 * (size_t)T) + a256(4 * (size_t)n) + a256((size_t)n) +
+  return kTwopassHead + 2 * a256(8 * (size_t)T) + a256(4 * (size_t)n) + a256((size_t)n) +
          a256(sizeof(uint2) * kMaxRuns * (size_t)n);
 }
 
@@ -585,7 +587,9 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   unsigned* status = dev_status ? dev_status : walk_counter + 1;
   int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
   unsigned* emit_counter = reinterpret_cast<unsigned*>(scratch + 16);
-  char* p = scratch + 256;
+  // the parallel scan takes up to kMaxSupers * kSuperTiles tiles; larger calls scan in one CTA
+  const bool par_scan = T <= (int64_t)kMaxSupers * kSuperTiles;
+  char* p = scratch + kTwopassHead;
   int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
   p += a256(8 * (size_t)T);
   int64_t* tile_prefix = reinterpret_cast<int64_t*>(p);
@@ -595,7 +599,7 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   uint8_t* nruns = reinterpret_cast<uint8_t*>(p);
   p += a256((size_t)n);
   uint2* runs = reinterpret_cast<uint2*>(p);
-  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead, s));
 
   const int mode = walk_mode(grid);
   const WalkArgs w{ro, rd, n, grid->view(), lat, counts, nruns, runs, tile_sum, walk_counter,
@@ -611,7 +615,11 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   }
   {
     KernelTimer kt("tile_scan", s);
-    tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_sum, T, tile_prefix, total, offsets + n);
+    if (par_scan)
+      tile_scan_par_kernel<<<(unsigned)((T + kSuperTiles - 1) / kSuperTiles), kSuperTiles, 0, s>>>(
+          tile_sum, T, tile_prefix, total, offsets + n);
+    else
+      tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_sum, T, tile_prefix, total, offsets + n);
   }
   HDDA_CUDA_TRY(cudaGetLastError());
   {

@@ -856,5 +856,58 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(
   }
 }
 
+
+// The same scan in parallel, for at most kMaxSupers * kSuperTiles tiles:
+// CTA b adds up every tile sum before its own kSuperTiles tiles (at most
+// (kMaxSupers - 1) loads per thread, eight in flight) and scans its own;
+// no CTA waits for another.
+constexpr int kSuperTiles = 1024;
+constexpr int kMaxSupers = 64;
+
+__global__ void __launch_bounds__(kSuperTiles) tile_scan_par_kernel(
+    const int64_t* __restrict__ tile_sum, int64_t T, int64_t* __restrict__ tile_prefix,
+    int64_t* __restrict__ total, int64_t* __restrict__ offsets_end) {
+  __shared__ int64_t wt[33];
+  __shared__ int64_t ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = blockIdx.x;
+  int64_t before = 0;
+#pragma unroll 8
+  for (int j = 0; j < b; ++j) before += tile_sum[(int64_t)j * kSuperTiles + threadIdx.x];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(kFull, before, o);
+  if (lane == 0) ws[warp] = before;
+  const int64_t i = (int64_t)b * kSuperTiles + threadIdx.x;
+  const int64_t x = i < T ? tile_sum[i] : 0;
+  int64_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wt[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int64_t t = wt[lane];
+    int64_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(kFull, ti, o);
+      if (lane >= o) ti += y;
+    }
+    wt[lane] = ti - t;
+    if (lane == 31) wt[32] = ti;
+  }
+  __syncthreads();
+  int64_t base = 0;
+#pragma unroll 8
+  for (int w = 0; w < kSuperTiles / 32; ++w) base += ws[w];
+  if (i < T) tile_prefix[i] = base + wt[warp] + inc - x;
+  if (b == (int)gridDim.x - 1 && threadIdx.x == 0) {
+    *total = base + wt[32];
+    *offsets_end = base + wt[32];
+  }
+}
+
 }  // namespace
 }  // namespace hdda
