@@ -83,6 +83,31 @@ __global__ void pack_dense_kernel(const uint8_t* __restrict__ dense, int L, int 
   if (w0 + lane < total) bits[w0 + lane] = mine;
 }
 
+// The 512 occupancy bits of the 8^3 block (bx, by, bz) of one level, voxel
+// ((x%8)*8 + y%8)*8 + z%8 at bit v%32 of word v/32: lane w < 16 receives word
+// w.  Every lane loads its 16 voxels first, so the loads are in flight
+// together, then the warp votes word by word.  Voxels past the grid's edge
+// are empty.
+__device__ __forceinline__ uint32_t block_words(const uint8_t* __restrict__ lvl, int R, int bx,
+                                                int by, int bz, int lane) {
+  uint32_t mine = 0;
+  // the 16 voxels of each lane first (loads in flight together), then the votes
+  uint8_t on[16];
+#pragma unroll
+  for (int w = 0; w < 16; ++w) {
+    const int v = w * 32 + lane;  // local voxel ((x%8)*8 + y%8)*8 + z%8
+    const int x = bx * 8 + (v >> 6), y = by * 8 + ((v >> 3) & 7), z = bz * 8 + (v & 7);
+    on[w] = 0;
+    if (x < R && y < R && z < R) on[w] = __ldg(lvl + ((int64_t)x * R + y) * R + z);
+  }
+#pragma unroll
+  for (int w = 0; w < 16; ++w) {
+    const uint32_t bal = __ballot_sync(kFull, on[w] != 0);
+    if (lane == w) mine = bal;
+  }
+  return mine;
+}
+
 __global__ void vdb_blocks_kernel(const uint8_t* __restrict__ dense, int L, int R, int B,
                                   uint32_t* __restrict__ blk_masks,
                                   uint8_t* __restrict__ blk_state) {
@@ -94,15 +119,7 @@ __global__ void vdb_blocks_kernel(const uint8_t* __restrict__ dense, int L, int 
   const int64_t b = warp % B3;
   const int bx = (int)(b / ((int64_t)B * B)), by = (int)((b / B) % B), bz = (int)(b % B);
   const uint8_t* lvl = dense + (int64_t)l * R * R * R;
-  uint32_t mine = 0;
-  for (int w = 0; w < 16; ++w) {
-    const int v = w * 32 + lane;  // local voxel ((x%8)*8 + y%8)*8 + z%8
-    const int x = bx * 8 + (v >> 6), y = by * 8 + ((v >> 3) & 7), z = bz * 8 + (v & 7);
-    bool on = false;
-    if (x < R && y < R && z < R) on = lvl[((int64_t)x * R + y) * R + z] != 0;
-    const uint32_t bal = __ballot_sync(kFull, on);
-    if (lane == w) mine = bal;
-  }
+  const uint32_t mine = block_words(lvl, R, bx, by, bz, lane);
   const bool any = __any_sync(kFull, lane < 16 && mine != 0u);
   const bool all = __all_sync(kFull, lane >= 16 || mine == kFull);
   if (lane < 16) blk_masks[warp * 16 + lane] = mine;
@@ -139,6 +156,9 @@ __device__ uint32_t cta_exclusive_scan(uint32_t v, uint32_t* warp_tot, uint32_t*
 // `gate` (null: always) lets an incremental update skip the kernel when no
 // block changed between empty, partial and full; the value is the same for
 // every thread of the launch.
+// A cell of a node beyond the grid's edge (never stored as a block state).
+constexpr uint8_t kBlockOutside = 0xff;
+
 __global__ void vdb_nodes_kernel(int L, int B, int N, const uint8_t* __restrict__ blk_state,
                                  uint32_t* __restrict__ child, uint32_t* __restrict__ tile,
                                  uint32_t* __restrict__ local_prefix,
@@ -158,16 +178,22 @@ __global__ void vdb_nodes_kernel(int L, int B, int N, const uint8_t* __restrict_
   const int nx = node / (N * N), ny = (node / N) % N, nz = node % N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t my_child = 0, my_tile = 0, my_in = 0;
+  // all 32 block states of this warp's words first (loads in flight together), then the votes
+  uint8_t st[32];
+#pragma unroll
   for (int j = 0; j < 32; ++j) {
     const int cell = (warp * 32 + j) * 32 + lane;
     const int bx = nx * 16 + (cell >> 8), by = ny * 16 + ((cell >> 4) & 15),
               bz = nz * 16 + (cell & 15);
-    const bool in = bx < B && by < B && bz < B;
-    uint8_t st = kBlockEmpty;
-    if (in) st = blk_state[(int64_t)l * B3 + ((int64_t)bx * B + by) * B + bz];
-    const uint32_t c = __ballot_sync(kFull, st == kBlockPartial);
-    const uint32_t t = __ballot_sync(kFull, st == kBlockFull);
-    const uint32_t i = __ballot_sync(kFull, in);
+    st[j] = kBlockOutside;
+    if (bx < B && by < B && bz < B)
+      st[j] = __ldg(blk_state + (int64_t)l * B3 + ((int64_t)bx * B + by) * B + bz);
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t c = __ballot_sync(kFull, st[j] == kBlockPartial);
+    const uint32_t t = __ballot_sync(kFull, st[j] == kBlockFull);
+    const uint32_t i = __ballot_sync(kFull, st[j] != kBlockOutside);
     if (lane == j) { my_child = c; my_tile = t; my_in = i; }
   }
   const int w = threadIdx.x;  // mask word 0..127
@@ -352,15 +378,7 @@ __global__ void vdb_update_blocks_kernel(const uint8_t* __restrict__ dense, int 
   const int64_t b = blk % B3;
   const int bx = (int)(b / ((int64_t)B * B)), by = (int)((b / B) % B), bz = (int)(b % B);
   const uint8_t* lvl = dense + (int64_t)l * R * R * R;
-  uint32_t mine = 0;
-  for (int w = 0; w < 16; ++w) {
-    const int v = w * 32 + lane;
-    const int x = bx * 8 + (v >> 6), y = by * 8 + ((v >> 3) & 7), z = bz * 8 + (v & 7);
-    bool on = false;
-    if (x < R && y < R && z < R) on = lvl[((int64_t)x * R + y) * R + z] != 0;
-    const uint32_t bal = __ballot_sync(kFull, on);
-    if (lane == w) mine = bal;
-  }
+  const uint32_t mine = block_words(lvl, R, bx, by, bz, lane);
   const uint32_t old = lane < 16 ? blk_masks[blk * kLeafWords + lane] : 0u;
   const bool diff = __any_sync(kFull, lane < 16 && mine != old);
   const bool any = __any_sync(kFull, lane < 16 && mine != 0u);
