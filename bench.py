@@ -301,6 +301,14 @@ def run_ours(args):
         hdda.render(O[c], D[c], gv, prm, field, out=rgba, status=status)
         return 0
 
+    def fused_step(j):
+        """The step's outputs (samples and frame) from hdda_traverse_composite: walk,
+        scan, then one kernel that stores each sample and composites it."""
+        c = cam_of(j)
+        gv.rebuild(dense)
+        hdda.traverse_composite(O[c], D[c], gv, prm, bufs, field, tstatus, rgba=rgba)
+        return totals[c]
+
     K, W = args.steps, args.warmup
     # clocks are sampled over every timed loop below (the headline loop alone is
     # shorter than a few sampling periods)
@@ -318,6 +326,7 @@ def run_ours(args):
     ms_ss, _, _, _ = timed(sampler_hdda_skip, max(3, K // 2), 2)
     ms_ds, _, _, _ = timed(sampler_dense_skip, max(3, K // 2), 2)
     ms_r, _, kern_r, _ = timed(render_step, K, 2, profile=True)
+    ms_f, _, kern_f, _ = timed(fused_step, K, 2, profile=True)
 
     # incremental rebuild: 1 % of the 8^3 blocks change (one voxel each, in partial
     # blocks, so the leaves are rewritten in place) and again 1 % with a new leaf each
@@ -603,6 +612,15 @@ def run_ours(args):
                                      "sample total back to the host before compositing",
                              "ms_per_step": round(ms_sync / max(3, K // 2), 4)},
         "incremental_update": upd,
+        "fused_step": {
+            "note": "vdb rebuild + hdda_traverse_composite: the walk and the tile scan, then one "
+                    "kernel that writes every sample at its CSR position and composites it (the "
+                    "same samples as the step, the render-only path's frame)",
+            "rays_per_s": round(n * K * world / (ms_f / 1e3), 1),
+            "ms_per_step": round(ms_f / K, 4),
+            "vs_step": round(ms / ms_f, 3),
+            "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}
+                        for k, v in kern_f.items()}},
         "render_only_step": {
             "note": "vdb rebuild + hdda_render: the walk, then runs expanded from the lattice "
                     "table and composited in one kernel; no sample, scan or host read-back",

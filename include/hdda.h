@@ -452,6 +452,33 @@ int hdda_render(const float* rays_o, const float* rays_d, int64_t n_rays,
                 int n_gauss, float* rgba_out, uint32_t* dev_status, hdda_stream_t stream);
 
 /*
+ * Sampling and compositing fused: the outputs of hdda_traverse_async and of
+ * hdda_render from one stream-ordered call (Algorithm 1's kept intervals,
+ * stored, and Sec. 1's accumulation over them).  The walk and the tile scan
+ * run as in the samplers; then one kernel expands each ray's runs, writes
+ * every sample at its CSR position and composites it, so the samples are
+ * written once and never read back.
+ *   rays_o, rays_d, n_rays, grid, params   as for hdda_traverse_async
+ *   offsets, ray_idx, t0, t1, capacity      as for hdda_traverse_async: the
+ *                same values bit for bit (capacity 0 writes the offsets
+ *                only, unclamped); a capacity below the total raises bit 2
+ *                of *dev_status, writes no sample at or past capacity and
+ *                clamps the offsets to capacity
+ *   field, n_gauss, rgba_out                as for hdda_render: the same
+ *                frame, bit for bit
+ *   dev_status   DEVICE uint32 (required, 4-byte aligned), as for
+ *                hdda_traverse_async
+ * Stream-ordered, no synchronisation except on the first use of a parameter
+ * set.  Scratch of about 150 bytes per ray comes from the stream-ordered
+ * allocator.
+ */
+int hdda_traverse_composite(const float* rays_o, const float* rays_d, int64_t n_rays,
+                            const hdda_grid* grid, const hdda_params* params, int64_t* offsets,
+                            int32_t* ray_idx, float* t0, float* t1, int64_t capacity,
+                            const float* field, int n_gauss, float* rgba_out,
+                            uint32_t* dev_status, hdda_stream_t stream);
+
+/*
  * Kernel timing and work counters for measurement, off by default; the
  * paper has no counterpart (it reports frame rates only).
  *   HDDA_PROFILE_TIMERS    every kernel the library launches is bracketed

@@ -19,6 +19,13 @@
 // (walk_from) and the next kMaxRuns runs are composited with its
 // transmittance and colour carried over, so samples are still accumulated
 // front to back.
+//
+// The same kernel with kStore also writes what the samplers' emit writes:
+// the CSR offsets (each task's 32-ray tile prefix from the tile scan plus a
+// warp scan of the tile's counts) and every sample at its CSR position (the
+// ray's offset, plus its samples of earlier rounds, plus its position in
+// this round), so one pass both stores the samples and composites them
+// (hdda_traverse_composite).
 #include "field.cuh"
 #include "walk.cuh"
 
@@ -32,11 +39,24 @@ constexpr uint32_t kNoRun = 0x7fffffffu;
 // Blob evaluations (sample x kept blob), counted only while profiling.
 __device__ unsigned long long g_render_evals;
 
-template <int kMode>
+// Outputs of the storing form (kStore): the samplers' CSR arrays.
+struct StoreArgs {
+  const int64_t* tile_prefix;  // exclusive prefix of the 32-ray tiles' sample counts
+  const int32_t* counts;       // samples per ray
+  int64_t* offsets;            // [n + 1], clamped to capacity
+  int32_t* ray_idx;
+  float* t0;
+  float* t1;
+  int64_t capacity;
+  unsigned* status;            // kDevCapacity when the samples do not fit
+};
+
+template <int kMode, bool kStore>
 __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, const uint8_t* __restrict__ nruns, const uint2* __restrict__ runs,
-    const float* __restrict__ field, int G, float* __restrict__ rgba, bool count_evals) {
+    const float* __restrict__ field, int G, float* __restrict__ rgba, bool count_evals,
+    StoreArgs out) {
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kRenderWarps)
   __shared__ float s_T[kRenderWarps][32];
   __shared__ float4 s_C[kRenderWarps][32];
@@ -63,6 +83,32 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   for (int j = 0; j < nr; ++j) sr[j * kRenderRays + lane] = __ldg(runs + (int64_t)j * n + r);
   int k_next = lat.K;  // where the ray's walk resumes
   if (nr_all > kMaxRuns) k_next = (int)sr[(kMaxRuns - 1) * kRenderRays + lane].y;
+  // storing form: lane i < kRenderRays holds ray i's CSR offset, then, per
+  // round, the output position of the round's position 0 of that ray
+  int64_t gofs = 0, gbase = 0;
+  if constexpr (kStore) {
+    const int64_t tile = task >> 2;  // four 8-ray tasks per 32-ray tile
+    const int64_t tr = tile * 32 + lane;
+    const int64_t c = tr < n ? (int64_t)__ldg(out.counts + tr) : 0;
+    int64_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const int64_t ex = __ldg(out.tile_prefix + tile) + inc - c;
+    const int first = (int)(task & 3) * kRenderRays;
+    gofs = __shfl_sync(kFull, ex, first + (lane & (kRenderRays - 1)));
+    const int64_t mine = __shfl_sync(kFull, c, first + (lane & (kRenderRays - 1)));
+    // capacity 0 counts only: offsets unclamped, no samples, no status
+    const bool clamp = out.capacity > 0;
+    if (has_ray) {
+      out.offsets[r] = clamp ? min(gofs, out.capacity) : gofs;
+      if (r == n - 1) out.offsets[n] = clamp ? min(gofs + mine, out.capacity) : gofs + mine;
+    }
+    if (__any_sync(kFull, clamp && has_ray && gofs + mine > out.capacity) && lane == 0)
+      atomicOr(out.status, kDevCapacity);
+  }
   for (;;) {
     // this round's runs: lengths, the warp's numbering, then first positions
     int cnt = 0;
@@ -78,6 +124,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     }
     const int pos = inc - cnt;
     const int W = __shfl_sync(kFull, inc, 31);
+    if constexpr (kStore) gbase = gofs - pos;
     if (lane < kRenderRays) {
       int q = pos;
       for (int j = 0; j < kMaxRuns; ++j) {
@@ -120,8 +167,17 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
         py = fmaf(tm, dy, oy);
         pz = fmaf(tm, dz, oz);
       }
+      if constexpr (kStore) {
+        const int64_t q = __shfl_sync(kFull, gbase, own) + p;
+        if (live && q < out.capacity) {
+          out.ray_idx[q] = (int32_t)(task * kRenderRays + own);
+          out.t0[q] = a0;
+          out.t1[q] = a1;
+        }
+      }
       evals += composite_chunk(fs, G, live, p + 1 >= W, own, px, py, pz, a0, a1, T_s, C_s);
     }
+    if constexpr (kStore) gofs += cnt;  // this round's samples of the lane's ray are written
     const bool more = k_next < lat.K;
     if (!__any_sync(kFull, more)) break;
     nr = 0;
@@ -193,16 +249,96 @@ int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* 
     const size_t fsm = field_smem_bytes(G, kRenderWarps);
     switch (mode) {
       case kModeDense:
-        render_kernel<kModeDense><<<nb, kRenderWarps * 32, fsm, s>>>(
-            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev);
+        render_kernel<kModeDense, false><<<nb, kRenderWarps * 32, fsm, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, StoreArgs{});
         break;
       case kModeVdb:
-        render_kernel<kModeVdb><<<nb, kRenderWarps * 32, fsm, s>>>(
-            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev);
+        render_kernel<kModeVdb, false><<<nb, kRenderWarps * 32, fsm, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, StoreArgs{});
         break;
       default:
-        render_kernel<kModeVdbRefined><<<nb, kRenderWarps * 32, fsm, s>>>(
-            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev);
+        render_kernel<kModeVdbRefined, false><<<nb, kRenderWarps * 32, fsm, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, StoreArgs{});
+        break;
+    }
+  }
+  HDDA_CUDA_TRY(cudaGetLastError());
+  return HDDA_OK;
+}
+
+// Scratch of the storing form: the header, tile sums and prefixes, counts,
+// run counts and runs.
+size_t sample_composite_scratch_bytes(int64_t n) {
+  const int64_t T = (n + 31) / 32;
+  return 256 + 2 * a256(8 * (size_t)T) + a256(4 * (size_t)n) + a256((size_t)n) +
+         a256(sizeof(uint2) * kMaxRuns * (size_t)n);
+}
+
+const char* sample_composite_name(int mode) {
+  return mode == kModeDense ? "dense_sample_composite"
+         : mode == kModeVdb ? "hdda_sample_composite_plain"
+                            : "hdda_sample_composite";
+}
+
+// Walk, tile scan, then the storing render kernel: the samplers' outputs and
+// the frame in one pass over the samples.
+int launch_sample_composite(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
+                            const LatticeDev& lat, const float* field, int G, float* rgba,
+                            int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
+                            int64_t capacity, unsigned* status, char* scratch, cudaStream_t s) {
+  const int64_t T = (n + 31) / 32;
+  unsigned* counter = reinterpret_cast<unsigned*>(scratch);
+  int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
+  char* p = scratch + 256;
+  int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
+  p += a256(8 * (size_t)T);
+  int64_t* tile_prefix = reinterpret_cast<int64_t*>(p);
+  p += a256(8 * (size_t)T);
+  int32_t* counts = reinterpret_cast<int32_t*>(p);
+  p += a256(4 * (size_t)n);
+  uint8_t* nr = reinterpret_cast<uint8_t*>(p);
+  p += a256((size_t)n);
+  uint2* runs = reinterpret_cast<uint2*>(p);
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+  const int mode = walk_mode(grid);
+  const WalkArgs w{ro, rd, n, grid->view(), lat, counts, nr, runs, tile_sum, counter, status};
+  const size_t stage = stage_layout(lat.K, w.g.L, w.g.R, grid->nodes_total(), mode).bytes;
+  {
+    KernelTimer kt(walk_name(mode), s);
+    const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
+    const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, skip, s)
+                   : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, skip, s)
+                                      : launch_walk_mode<kModeVdbRefined>(w, stage, skip, s);
+    if (st != HDDA_OK) return st;
+  }
+  {
+    KernelTimer kt("tile_scan", s);
+    if (T <= (int64_t)kMaxSupers * kSuperTiles)
+      tile_scan_par_kernel<<<(unsigned)((T + kSuperTiles - 1) / kSuperTiles), kSuperTiles, 0, s>>>(
+          tile_sum, T, tile_prefix, total, offsets + n);
+    else
+      tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_sum, T, tile_prefix, total, offsets + n);
+  }
+  HDDA_CUDA_TRY(cudaGetLastError());
+  {
+    KernelTimer kt(sample_composite_name(mode), s);
+    const int64_t warps = (n + kRenderRays - 1) / kRenderRays;
+    const unsigned nb = (unsigned)((warps + kRenderWarps - 1) / kRenderWarps);
+    const bool ev = counters_on();
+    const size_t fsm = field_smem_bytes(G, kRenderWarps);
+    const StoreArgs out{tile_prefix, counts, offsets, ray_idx, t0, t1, capacity, status};
+    switch (mode) {
+      case kModeDense:
+        render_kernel<kModeDense, true><<<nb, kRenderWarps * 32, fsm, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, out);
+        break;
+      case kModeVdb:
+        render_kernel<kModeVdb, true><<<nb, kRenderWarps * 32, fsm, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, out);
+        break;
+      default:
+        render_kernel<kModeVdbRefined, true><<<nb, kRenderWarps * 32, fsm, s>>>(
+            ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, out);
         break;
     }
   }
@@ -268,4 +404,52 @@ extern "C" int hdda_render(const float* rays_o, const float* rays_d, int64_t n_r
   HDDA_CUDA_TRY(cudaStreamSynchronize(s));
   if (*hw & kDevInternal) return set_error(HDDA_ERR_INTERNAL, "region check failed on the device");
   return HDDA_OK;
+}
+
+extern "C" int hdda_traverse_composite(const float* rays_o, const float* rays_d, int64_t n_rays,
+                                       const hdda_grid* grid, const hdda_params* params,
+                                       int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
+                                       int64_t capacity, const float* field, int n_gauss,
+                                       float* rgba_out, uint32_t* dev_status,
+                                       hdda_stream_t stream) {
+  using namespace hdda;
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!grid) return set_error(HDDA_ERR_INVALID_ARG, "grid is NULL");
+  if (!params) return set_error(HDDA_ERR_INVALID_ARG, "params is NULL");
+  if (n_rays < 0 || n_rays > INT32_MAX)
+    return set_error(HDDA_ERR_INVALID_ARG, "n_rays=%lld", (long long)n_rays);
+  if (n_gauss < 0 || n_gauss > kMaxGauss)
+    return set_error(HDDA_ERR_INVALID_ARG, "n_gauss=%d outside 0..%d", n_gauss, kMaxGauss);
+  if (!offsets) return set_error(HDDA_ERR_INVALID_ARG, "offsets is NULL");
+  if (capacity < 0) return set_error(HDDA_ERR_INVALID_ARG, "capacity < 0");
+  if (capacity > 0 && (!ray_idx || !t0 || !t1))
+    return set_error(HDDA_ERR_INVALID_ARG, "sample arrays NULL");
+  if (n_rays > 0 && (!rays_o || !rays_d || !rgba_out))
+    return set_error(HDDA_ERR_INVALID_ARG, "NULL pointer");
+  if (n_gauss > 0 && !field) return set_error(HDDA_ERR_INVALID_ARG, "field is NULL");
+  if (reinterpret_cast<uintptr_t>(rgba_out) % 16 != 0)
+    return set_error(HDDA_ERR_INVALID_ARG, "rgba_out must be 16-byte aligned");
+  if (!dev_status) return set_error(HDDA_ERR_INVALID_ARG, "dev_status is NULL");
+  if (reinterpret_cast<uintptr_t>(dev_status) % 4 != 0)
+    return set_error(HDDA_ERR_INVALID_ARG, "dev_status must be 4-byte aligned");
+  int dev = 0;
+  HDDA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != grid->device)
+    return set_error(HDDA_ERR_INVALID_ARG, "grid lives on device %d, current is %d",
+                     grid->device, dev);
+  LatticeDev lat;
+  int st = lattice_for(params, s, &lat);
+  if (st != HDDA_OK) return st;
+  if (n_rays == 0) {
+    HDDA_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
+    return HDDA_OK;
+  }
+  char* scratch = nullptr;
+  HDDA_CUDA_TRY(cudaMallocAsync(&scratch, sample_composite_scratch_bytes(n_rays), s));
+  st = launch_sample_composite(rays_o, rays_d, n_rays, grid, lat, field, n_gauss, rgba_out,
+                               offsets, ray_idx, t0, t1, capacity, dev_status, scratch, s);
+  cudaError_t e = cudaFreeAsync(scratch, s);
+  if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
+  return st;
 }

@@ -31,7 +31,7 @@ EXPORTED = [
     "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine", "hdda_batch_create",
     "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free", "hdda_grid_set_walk",
     "hdda_render", "hdda_grid_update", "hdda_traverse_async", "hdda_set_region_checks",
-    "hdda_region_checks",
+    "hdda_region_checks", "hdda_traverse_composite",
 ]
 
 
@@ -121,6 +121,8 @@ def load(path: str | None = None):
     lib.hdda_render.argtypes = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, i32, vp, vp, vp]
     lib.hdda_traverse_async.argtypes = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, vp, vp, vp,
                                         i64, vp, vp]
+    lib.hdda_traverse_composite.argtypes = [vp, vp, i64, vp, ctypes.POINTER(Params), vp, vp, vp,
+                                            vp, i64, vp, i32, vp, vp, vp]
     lib.hdda_profiler_enable.argtypes = [i32]
     lib.hdda_profiler_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
     for name in EXPORTED:
@@ -343,6 +345,29 @@ def traverse_async(rays_o, rays_d, grid: Grid, params: Params, out: Samples,
                                       _stream(stream)))
     out.total = -1
     return out
+
+
+def traverse_composite(rays_o, rays_d, grid: Grid, params: Params, out: Samples, field,
+                       status: torch.Tensor, rgba: torch.Tensor | None = None,
+                       stream=None) -> torch.Tensor:
+    """Sampling and compositing fused (hdda_traverse_composite): writes the
+    samples traverse_async writes into `out` and returns the frame render
+    gives, from one stream-ordered call.  `status` as for traverse_async."""
+    ro = _cuda(rays_o, torch.float32, (-1, 3))
+    rd = _cuda(rays_d, torch.float32, (-1, 3))
+    f = _cuda(field, torch.float32, (-1, 8))
+    if not status.is_cuda or status.numel() < 1 or status.element_size() != 4:
+        raise ValueError("status must be a CUDA tensor of 4-byte elements")
+    n = int(ro.shape[0])
+    if rgba is None:
+        rgba = torch.empty((n, 4), dtype=torch.float32, device=ro.device)
+    _hold(stream, ro, rd, f, out.offsets, out.ray_idx, out.t0, out.t1, status, rgba)
+    _check(load().hdda_traverse_composite(
+        _ptr(ro), _ptr(rd), n, grid.handle, ctypes.byref(params), _ptr(out.offsets),
+        _ptr(out.ray_idx), _ptr(out.t0), _ptr(out.t1), int(out.t0.numel()), _ptr(f),
+        int(f.shape[0]), _ptr(rgba), status.data_ptr(), _stream(stream)))
+    out.total = -1
+    return rgba
 
 
 def traverse_hdda(rays_o, rays_d, grid: Grid, params: Params, out: Samples | None = None,
