@@ -47,7 +47,8 @@ KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # from the same ncu --set full captures (object frame, camera 0); dropped like the traffic
 # when a kernel changes.
 PROFILED_COUNTERS = {
-    "object": {"hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98},
+    "object": {"hdda_walk": {"l2_hit_pct": 37.6, "active_lanes_of_32": 24.59},
+               "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98},
                "composite": {"l2_hit_pct": 36.5, "active_lanes_of_32": 31.92}},
 }
 # DRAM bytes (read + write) per launch from ncu --set full of a workload's step on
@@ -55,8 +56,9 @@ PROFILED_COUNTERS = {
 # roofline's "traffic"; an entry must be dropped whenever its kernel changes, and a
 # workload without a capture reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 237_030_400, "hdda_emit": 269_582_080},
-    "unbounded": {"composite": 1_502_856_960, "hdda_emit": 2_182_746_624},
+    "object": {"composite": 237_030_400, "hdda_emit": 269_582_080, "hdda_walk": 15_695_104},
+    "unbounded": {"composite": 1_502_856_960, "hdda_emit": 2_182_746_624,
+                  "hdda_walk": 26_170_880},
 }
 
 
