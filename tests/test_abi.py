@@ -68,3 +68,28 @@ def test_region_check_switch_is_host_only(libpath):
         assert lib.hdda_set_region_checks(0) == 0 and lib.hdda_region_checks() == 0
     finally:
         lib.hdda_set_region_checks(before)
+
+
+def test_argument_errors_are_status_codes_before_any_device_call(libpath):
+    """Invalid arguments come back as HDDA_ERR_INVALID_ARG with a message,
+    checked before the library touches a device (so this runs without one)."""
+    lib = ctypes.CDLL(libpath)
+    lib.hdda_last_error.restype = ctypes.c_char_p
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    invalid = 1
+    null = vp(None)
+    # stream-ordered sampler without a status word
+    assert lib.hdda_traverse_async(null, null, i64(0), null, null, null, null, null, null,
+                                   i64(0), null, null) == invalid
+    assert b"dev_status" in lib.hdda_last_error()
+    # render-only path and fused sampler + compositor without a grid
+    assert lib.hdda_render(null, null, i64(0), null, null, null, 0, null, null, null) == invalid
+    assert b"grid" in lib.hdda_last_error()
+    assert lib.hdda_traverse_composite(null, null, i64(0), null, null, null, null, null, null,
+                                       i64(0), null, 0, null, null, null) == invalid
+    assert b"grid" in lib.hdda_last_error()
+    # compositor with a negative ray count and with too many blobs
+    assert lib.hdda_composite(null, null, i64(-1), null, null, null, null, 0, null, null) == invalid
+    assert lib.hdda_composite(null, null, i64(1), null, null, null, null, 100000, null,
+                              null) == invalid
+    assert b"n_gauss" in lib.hdda_last_error()
