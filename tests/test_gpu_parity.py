@@ -10,6 +10,7 @@ import torch
 
 import oracle
 from paper_2404_10272_gb300 import scenes
+import _layout
 from _helpers import assert_same, gpu_samples, oracle_samples, subset_rays, to_np
 
 pytestmark = pytest.mark.gpu
@@ -205,7 +206,7 @@ def test_grid_structures_match_oracle(H):
     st = gv.stats()
     assert st.n_leaves == v["n_leaves"] and st.n_tiles == v["n_tiles"]
     assert st.dense_bytes == 3 * oracle.dense_words_per_level(37) * 4
-    nsuper, lsub = oracle.vdb_refinement(v)
+    nsuper, lsub = _layout.vdb_refinement(v)
     np.testing.assert_array_equal(gv.array(H.ARRAY_NODE_SUPER), nsuper.reshape(-1))
     np.testing.assert_array_equal(gv.array(H.ARRAY_LEAF_SUB), lsub.reshape(-1))
     # leaf prefix: global index of the first leaf of each child-mask word

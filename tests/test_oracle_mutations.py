@@ -31,16 +31,27 @@ MUTANTS = {
                             "            k += 1;\n            t = near_t + (float)k * step;"),
     "transmittance_not_updated": ("T *= 1.0 - alpha;", ""),
     "colour_not_weighted_by_T": ("C[c] += T * alpha * (wc[c] / sigma);", "C[c] += alpha * (wc[c] / sigma);"),
+    # the compositor's field (Sec. 1's accumulation over a sum of Gaussian blobs)
+    "falloff_without_factor_2": ("exp(-d2 / (2.0 * sg * sg))", "exp(-d2 / (sg * sg))"),
+    "amplitude_dropped": ("double w = (double)G[4] * exp(", "double w = exp("),
+    "colour_not_weighted_by_density": [
+        ("wc[c] += w * (double)G[5 + c];", "wc[c] += (double)G[5 + c];"),
+        ("C[c] += T * alpha * (wc[c] / sigma);", "C[c] += T * alpha * (wc[c] / n_g);")],
+    "field_at_interval_start": ("double tm = 0.5 * (a0 + a1);", "double tm = a0;"),
+    "alpha_without_interval_length": ("-expm1(-sigma * (a1 - a0))", "-expm1(-sigma)"),
 }
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_mutant(name):
-    old, new = MUTANTS[name]
+    edits = MUTANTS[name]
+    if isinstance(edits, tuple):
+        edits = [edits]
     src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
-    src = src.replace(old, new)
+    for old, new in edits:
+        assert src.count(old) >= 1, f"mutation anchor for {name} not found: {old!r}"
+        src = src.replace(old, new)
     with tempfile.TemporaryDirectory() as tmp:
         c = os.path.join(tmp, "m.c")
         so = os.path.join(tmp, "m.so")

@@ -319,24 +319,42 @@ def test_vdb_round_trip_and_counts(res, p):
     assert not np.any(v["child"] & v["tile"])
 
 
-def test_vdb_refinement_masks_single_voxel():
-    # voxel (5, 9, 40) of a 64^3 grid: 32^3 group (0, 0, 1) -> bit 1 of word 0; 16^3 group
-    # (0, 0, 2) -> bit 2 of word 2; in its leaf, local (5, 1, 0): 2^3 cell (2, 0, 0) -> bit 32,
-    # i.e. bit 0 of word 1; 4^3 cell (1, 0, 0) -> bit 4 of word 2
-    occ = np.zeros((1, 64, 64, 64), np.uint8)
-    occ[0, 5, 9, 40] = 1
-    v = oracle.build_vdb(occ)
-    ns, ls = oracle.vdb_refinement(v)
-    assert ns.shape == (1, 1, 18)
-    assert ns[0, 0, 0] == 1 << 1 and ns[0, 0, 1] == 0
-    assert ns[0, 0, 2] == 1 << 2 and not ns[0, 0, 3:].any()
-    assert ls.tolist() == [[0, 1, 1 << 4, 0, 0]]
-    # the whole 2^3 cell (4..5, 8..9, 40..41) occupied: the same cell is also full,
-    # bit 32 of the full-cell words (bit 0 of word 4)
-    occ[0, 4:6, 8:10, 40:42] = 1
-    _, ls = oracle.vdb_refinement(oracle.build_vdb(occ))
-    assert ls.tolist() == [[0, 1, 1 << 4, 0, 1]]
-    # one voxel less: occupied but no longer full
-    occ[0, 4, 8, 40] = 0
-    _, ls = oracle.vdb_refinement(oracle.build_vdb(occ))
-    assert ls.tolist() == [[0, 1, 1 << 4, 0, 0]]
+def _one_sample(field, o, d, t0, t1):
+    o = np.array([o], np.float32)
+    d = np.array([d], np.float32)
+    return oracle.composite(o, d, np.array([0, 1], np.int64), np.array([t0], np.float32),
+                            np.array([t1], np.float32), np.array(field, np.float32))[0]
+
+
+@pytest.mark.parametrize("o,dist2", [
+    ((-1.0, 0.5, 0.0), 0.25),      # midpoint (0, 0.5, 0): one radius off the centre
+    ((-1.0, 1.0, 0.0), 1.0),       # (0, 1, 0): two radii
+    ((-1.5, 0.0, 0.0), 0.25),      # (-0.5, 0, 0): one radius along the ray's own axis
+    ((-0.75, 0.25, 0.25), 0.1875),  # (0.25, 0.25, 0.25): all three components
+])
+def test_composite_gaussian_falloff(o, dist2):
+    # One blob of amplitude a and radius s at the origin, one interval [0.75, 1.25] along +x
+    # whose midpoint (t = 1) lies at squared distance dist2 from the centre: the density is
+    # a * exp(-dist2 / (2 s^2)) (Sec. 1's field; the Gaussian's 2 s^2), the colour the blob's
+    # own, and the pixel (1 - exp(-sigma * dt)) * rgb with dt = 0.5.  Every input and the
+    # midpoint are exact in binary32.
+    a, s, rgb = 4.0, 0.5, np.array([0.25, 0.5, 0.75])
+    px = _one_sample([[0, 0, 0, s, a, *rgb]], o, (1, 0, 0), 0.75, 1.25)
+    sigma = a * math.exp(-dist2 / (2 * s * s))
+    alpha = 1 - math.exp(-sigma * 0.5)
+    np.testing.assert_allclose(px, [*(alpha * rgb), alpha], rtol=1e-12)
+
+
+def test_composite_colour_is_density_weighted_mean():
+    # Two blobs seen from one point at different distances: weights w1 = a1 e^(-1/2) (one
+    # radius) and w2 = a2 e^(-2) (two radii).  The density is w1 + w2 and the colour the
+    # density-weighted mean (w1 rgb1 + w2 rgb2) / (w1 + w2), not the plain mean of the two.
+    rgb1, rgb2 = np.array([1.0, 0.0, 0.5]), np.array([0.0, 1.0, 0.25])
+    field = [[0, 0, 0, 0.5, 2.0, *rgb1], [0, 1.5, 0, 0.5, 3.0, *rgb2]]
+    px = _one_sample(field, (-1, 0.5, 0), (1, 0, 0), 0.75, 1.25)   # midpoint (0, 0.5, 0)
+    w1, w2 = 2.0 * math.exp(-0.5), 3.0 * math.exp(-2.0)
+    colour = (w1 * rgb1 + w2 * rgb2) / (w1 + w2)
+    alpha = 1 - math.exp(-(w1 + w2) * 0.5)
+    np.testing.assert_allclose(px, [*(alpha * colour), alpha], rtol=1e-12)
+    # the plain mean differs by far more than the tolerance
+    assert np.abs(alpha * (rgb1 + rgb2) / 2 - px[:3]).max() > 0.05
