@@ -177,7 +177,9 @@ def run_ours(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        # replicas only: no data path crosses GPUs; a host (gloo) group carries just the
+        # barrier around the timed loops and the MAX of the ranks' elapsed times
+        dist.init_process_group("gloo")
     import __graft_entry__
     __graft_entry__.build()
     from paper_2404_10272_gb300 import hdda, replicas, scenes
@@ -290,7 +292,7 @@ def run_ours(args):
             hdda.profiler_enable(False)
             kern = hdda.profiler_read()
         clk = clocks.stop() if clocks else None
-        ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), device="cuda")
+        ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
         return ms, samples, kern, clk
 
     status = torch.zeros(1, dtype=torch.int32, device="cuda")

@@ -334,8 +334,9 @@ int hdda_traverse_async(const float* rays_o, const float* rays_d, int64_t n_rays
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) and should come before any stream capture.  All
  * calls share the array: calls whose GPU work overlaps race on it and must
- * be serialised by the caller.  Synchronises the stream twice (lattice
- * length, sample total); every output is complete when it returns.
+ * be serialised by the caller.  Every call, not only the first, synchronises
+ * the stream twice (lattice length, sample total); every output is complete
+ * when it returns.
  */
 int hdda_traverse_hdda_noalloc(const float* rays_o, const float* rays_d, int64_t n_rays,
                                const hdda_grid* grid, const hdda_params* params,

@@ -86,7 +86,7 @@ struct LatticeDev {
 };
 
 // Bytes of one lattice block of capacity max_k: t, tm, kidx and hdr.
-__host__ __device__ inline size_t lattice_block_bytes(int max_k) {
+__host__ __device__ constexpr size_t lattice_block_bytes(int max_k) {
   return (sizeof(float) * (2 * (size_t)max_k + 1) + sizeof(int) * (kKidxMax + 2) + 16 + 255) &
          ~(size_t)255;
 }
@@ -144,8 +144,12 @@ class KernelTimer {
 // Traversal over scratch memory the caller provides instead of memory the
 // library allocates (traverse.cu).  `scratch` is device memory of at least
 // traverse_scratch_bytes(max_k, max_tiles) bytes, 256-byte aligned; nothing
-// is allocated.  Rays per tile: traverse_rays_per_tile().
-size_t traverse_scratch_bytes(int max_k, int64_t max_tiles);
+// is allocated.  Rays per tile: traverse_rays_per_tile().  Layout: 256 bytes
+// of lattice read-back words, one lattice block of capacity max_k, then the
+// one-pass sampler's 32-byte header and one 8-byte state per tile.
+constexpr size_t traverse_scratch_bytes(int max_k, int64_t max_tiles) {
+  return 256 + lattice_block_bytes(max_k) + 32 + 8 * (size_t)max_tiles;
+}
 // Validates params and returns the cached device lattice for them (traverse.cu).
 int lattice_for(const hdda_params* p, cudaStream_t s, LatticeDev* out);
 int64_t traverse_rays_per_tile();

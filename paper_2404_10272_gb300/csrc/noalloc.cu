@@ -26,9 +26,12 @@ namespace {
 
 constexpr int kStaticMaxCandidates = 16384;            // lattice candidates per ray
 constexpr int64_t kStaticMaxTiles = 16384;             // CTAs of 128 rays: 2,097,152 rays
-constexpr size_t kStaticScratchBytes =
-    256 + ((sizeof(float) * (2 * (size_t)kStaticMaxCandidates + 1) + 255) & ~(size_t)255) +
-    2 * sizeof(int64_t) * (size_t)kStaticMaxTiles;     // 393,728 bytes
+constexpr size_t kStaticScratchBytes = 393728;         // the documented size
+// The array must hold the traversal's scratch layout at the maximum sizes; a
+// change to that layout that outgrows it fails to compile here.
+static_assert(hdda::traverse_scratch_bytes(kStaticMaxCandidates, kStaticMaxTiles) <=
+                  kStaticScratchBytes,
+              "static scratch smaller than the traversal's layout at its maximum sizes");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -63,9 +66,6 @@ extern "C" int hdda_traverse_hdda_noalloc(const float* rays_o, const float* rays
                                           int64_t capacity, int64_t* total_out,
                                           hdda_stream_t stream) {
   hdda::clear_error();
-  static_assert(kStaticScratchBytes == 393728, "documented size");
-  if (hdda::traverse_scratch_bytes(kStaticMaxCandidates, kStaticMaxTiles) > kStaticScratchBytes)
-    return hdda::set_error(HDDA_ERR_INTERNAL, "static scratch layout mismatch");
   void* scratch = nullptr;
   int st = static_scratch(&scratch);
   if (st != HDDA_OK) return st;

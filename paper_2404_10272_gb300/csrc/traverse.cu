@@ -717,12 +717,9 @@ int lattice_for(const hdda_params* p, cudaStream_t s, LatticeDev* out) {
 // ---------------------------------------------------------------------------
 // traversal over caller-provided scratch (no allocation of any kind)
 // ---------------------------------------------------------------------------
-// Scratch layout: [0, 256) lattice read-back words; then one lattice block
-// of capacity max_k; then the sampler's 32-byte header and tile states.
-
-size_t traverse_scratch_bytes(int max_k, int64_t max_tiles) {
-  return 256 + lattice_block_bytes(max_k) + 32 + 8 * (size_t)max_tiles;
-}
+// Scratch layout (traverse_scratch_bytes): [0, 256) lattice read-back words;
+// then one lattice block of capacity max_k; then the sampler's 32-byte
+// header and tile states.
 
 int64_t traverse_rays_per_tile() { return kBS; }
 

@@ -8,7 +8,7 @@ data exchange (weak scaling).  This module holds the host side of that:
 * the slowest rank's elapsed time: the only collective, a MAX all-reduce;
 * the aggregate rate over all ranks.
 
-It runs on any torch.distributed backend (NCCL on GPUs, gloo in tests).
+It runs on a host (gloo) process group: nothing on the data path crosses GPUs.
 """
 from __future__ import annotations
 

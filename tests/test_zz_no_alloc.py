@@ -6,15 +6,18 @@ never enter the CUDA allocator.  hdda_traverse_hdda_noalloc serves them by
 keeping its scratch in a fixed device array inside the library.  These tests
 call it through the C ABI and check that two calls in a row give exactly the
 samples of hdda_traverse_hdda (the suite's bar for samples is bit equality),
-and that sizes beyond its fixed limits are refused with a clear error.  The
-file is named so that pytest runs it after every other test.
+and that sizes beyond its fixed limits are refused with a clear error.  Its
+own paths are checked against the oracle too: rays with more runs than its
+CTAs keep (they walk again and write their own samples) and the largest
+single-GPU frame.  The file is named so that pytest runs it after every other
+test.
 """
 import numpy as np
 import pytest
 import torch
 
 from paper_2404_10272_gb300 import scenes
-from _helpers import assert_same, to_np
+from _helpers import assert_same, oracle_samples, slab_scene, subset_rays, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -87,3 +90,47 @@ def test_limits_are_refused(H):
                                   prm, out)
     assert got.total == ref.total
     np.testing.assert_array_equal(to_np(got.offsets), to_np(ref.offsets))
+
+
+def test_rays_with_many_runs_against_oracle(H):
+    # Slabs every other voxel: most rays cross more runs than a CTA keeps in shared memory
+    # (16), so the one-pass kernel re-walks them and writes their samples itself.  The
+    # samples must still be the oracle's, bit for bit, on two calls in a row.
+    occ, aabbs, o, d, _, p = slab_scene(128, 2, 700, 7128)
+    want = oracle_samples(o, d, occ, aabbs, p)
+    off, _, t0, t1 = want
+    runs = np.array([1 + int(np.sum(t0[off[r] + 1:off[r + 1]] != t1[off[r]:off[r + 1] - 1]))
+                     if off[r + 1] > off[r] else 0 for r in range(o.shape[0])])
+    assert (runs > 16).mean() > 0.5
+    grid = H.build_vdb(torch.from_numpy(occ).cuda(), aabbs)
+    ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    prm = _params(H, p)
+    out = H.alloc_samples(o.shape[0], int(off[-1]))
+    for call in range(2):
+        out.t0.fill_(float("nan"))
+        got = H.traverse_hdda_noalloc(ot, dt, grid, prm, out)
+        torch.cuda.synchronize()
+        assert_same(tuple(to_np(x) for x in got.trimmed()), want, f"many runs, call {call}")
+
+
+def test_full_unbounded_frame(H):
+    # The largest single-GPU frame (4 x 128^3 cascade, 1245 x 825 rays, growing step): all
+    # samples equal the allocating sampler's, and a stratified subset of rays (every 97th)
+    # equals the oracle's.
+    sc = scenes.unbounded_scene()
+    o, d = scenes.unbounded_camera().rays()
+    grid, ot, dt, prm, ref = _case(H, sc, o, d)
+    out = H.alloc_samples(o.shape[0], ref.total)
+    got = H.traverse_hdda_noalloc(ot, dt, grid, prm, out)
+    torch.cuda.synchronize()
+    assert got.total == ref.total
+    g_off, g_idx, g_t0, g_t1 = (to_np(x) for x in got.trimmed())
+    assert_same((g_off, g_idx, g_t0, g_t1), tuple(to_np(x) for x in ref.trimmed()),
+                "noalloc unbounded frame")
+    so, sd, sel = subset_rays(o, d, 97, 5)
+    want = oracle_samples(so, sd, sc.occ, sc.aabbs, sc.params)
+    idx = np.concatenate([np.arange(g_off[r], g_off[r + 1]) for r in sel])
+    sub_off = np.concatenate([[0], np.cumsum(g_off[sel + 1] - g_off[sel])])
+    sub_idx = np.repeat(np.arange(sel.size, dtype=np.int32), np.diff(sub_off))
+    assert np.array_equal(g_idx[idx], np.repeat(sel, np.diff(sub_off)))
+    assert_same((sub_off, sub_idx, g_t0[idx], g_t1[idx]), want, "noalloc unbounded subset")
