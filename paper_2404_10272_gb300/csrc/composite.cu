@@ -4,12 +4,14 @@
 // per-chunk accumulation are in field.cuh.
 //
 // Work split: a warp owns kRaysPerWarp consecutive rays, whose samples are
-// one contiguous range of the CSR arrays, and walks that range 32 samples at
-// a time, one sample per lane, so every lane has work whatever the rays'
+// one contiguous range of the CSR arrays, and walks that range 64 samples at
+// a time, two per lane (field.cuh), so every lane has work whatever the rays'
 // lengths.  One warp per task and small CTAs let the hardware scheduler
 // balance tasks of uneven cost; tasks of 4 rays (about 170 samples in the
-// object-centric frame, 750 in the unbounded one) keep the last tasks short,
-// measured faster than 8, 16 or 2.
+// object-centric frame, 750 in the unbounded one) keep the last tasks short.
+// The task's rays (origin, direction) are staged in shared memory, and
+// every lane keeps the rays' first sample positions in registers, so a
+// sample finds its ray by three compares.
 #include "field.cuh"
 
 namespace hdda {
@@ -27,22 +29,26 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
     const int64_t* __restrict__ offsets, const float* __restrict__ t0,
     const float* __restrict__ t1, const float* __restrict__ field, int G,
     float* __restrict__ rgba, bool count_evals) {
+  static_assert(kRaysPerWarp == 4, "the owner lookup below compares against three ray starts");
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kWarpsPerCta)
-  __shared__ float s_T[kWarpsPerCta][32];
-  __shared__ float4 s_C[kWarpsPerCta][32];
+  __shared__ float s_T[kWarpsPerCta][kRaysPerWarp];
+  __shared__ float4 s_C[kWarpsPerCta][kRaysPerWarp];
+  __shared__ float4 s_ray[kWarpsPerCta][kRaysPerWarp][2];  // {o, d.x}, {d.y, d.z, -, -}
   const FieldSmem fs = stage_blobs(smem, field, G);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* T_s = s_T[wib];
   float4* C_s = s_C[wib];
+  float4 (*rs)[2] = s_ray[wib];
   unsigned long long evals = 0;  // this warp's blob evaluations
   const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (wg * kRaysPerWarp < n) {
-    const int64_t r = wg * kRaysPerWarp + lane;
-    const bool has_ray = lane < kRaysPerWarp && r < n;
-    const int64_t rr = has_ray ? r : min(wg * kRaysPerWarp + kRaysPerWarp, n);
-    const int64_t sb = offsets[rr];
-    const int64_t se = has_ray ? offsets[r + 1] : sb;
+  if (wg * kRaysPerWarp >= n) return;  // uniform per warp; no block barrier follows
+  const int64_t r = wg * kRaysPerWarp + lane;
+  const bool has_ray = lane < kRaysPerWarp && r < n;
+  const int64_t rr = has_ray ? r : min(wg * kRaysPerWarp + kRaysPerWarp, n);
+  const int64_t sb = offsets[rr];
+  const int64_t se = has_ray ? offsets[r + 1] : sb;
+  if (lane < kRaysPerWarp) {
     float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
     if (has_ray) {
 #pragma unroll
@@ -51,55 +57,64 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
         d[c] = __ldg(rd + 3 * r + c);
       }
     }
+    rs[lane][0] = make_float4(o[0], o[1], o[2], d[0]);
+    rs[lane][1] = make_float4(d[1], d[2], 0.f, 0.f);
     T_s[lane] = 1.f;
     C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
-    const int64_t wbeg = __shfl_sync(kFull, sb, 0);
-    const int64_t wend = __shfl_sync(kFull, se, 31);
-    const int sbr = (int)(sb - wbeg);  // a warp's samples fit in 32 bits (4 rays)
-    // the next chunk's interval ends are loaded one chunk ahead, so their
-    // DRAM latency overlaps the current chunk's field evaluation
-    float n0 = 0.f, n1 = 0.f;
-    if (wbeg + lane < wend) {
-      n0 = __ldg(t0 + wbeg + lane);
-      n1 = __ldg(t1 + wbeg + lane);
-    }
-    for (int64_t base = wbeg; base < wend; base += 32) {
-      const int64_t p = base + lane;
-      const bool live = p < wend;
-      const float c0 = n0, c1 = n1;
-      if (p + 32 < wend) {
-        n0 = __ldg(t0 + p + 32);
-        n1 = __ldg(t1 + p + 32);
-      }
-      const int pr = (int)(p - wbeg);
-      int own = 0;  // the last ray slot whose first sample is <= p
-#pragma unroll
-      for (int s = kRaysPerWarp / 2; s > 0; s >>= 1) {
-        const int v = __shfl_sync(kFull, sbr, own + s);
-        if (v <= pr) own += s;
-      }
-      const float ox = __shfl_sync(kFull, o[0], own), oy = __shfl_sync(kFull, o[1], own),
-                  oz = __shfl_sync(kFull, o[2], own);
-      const float dx = __shfl_sync(kFull, d[0], own), dy = __shfl_sync(kFull, d[1], own),
-                  dz = __shfl_sync(kFull, d[2], own);
-      float a0 = 0.f, a1 = 0.f, px = 0.f, py = 0.f, pz = 0.f;
-      if (live) {
-        a0 = c0;
-        a1 = c1;
-        const float tm = 0.5f * (a0 + a1);
-        px = fmaf(tm, dx, ox);
-        py = fmaf(tm, dy, oy);
-        pz = fmaf(tm, dz, oz);
-      }
-      evals += composite_chunk(fs, G, live, p + 1 >= wend, own, px, py, pz, a0, a1, T_s, C_s);
-    }
-    if (has_ray) {
-      const float4 acc = C_s[lane];
-      reinterpret_cast<float4*>(rgba)[r] = make_float4(acc.x, acc.y, acc.z, 1.f - T_s[lane]);
-    }
-    if (count_evals && lane == 0) atomicAdd(&g_blob_evals, evals);
   }
+  __syncwarp();
+  const int64_t wbeg = __shfl_sync(kFull, sb, 0);
+  const int64_t wend = __shfl_sync(kFull, se, kRaysPerWarp - 1);
+  // first sample of rays 1..3 relative to the warp's first sample (a task's
+  // samples fit in 32 bits)
+  const int s1 = (int)(__shfl_sync(kFull, sb, 1) - wbeg), s2 = (int)(__shfl_sync(kFull, sb, 2) - wbeg),
+            s3 = (int)(__shfl_sync(kFull, sb, 3) - wbeg);
+  const int total = (int)(wend - wbeg);
+  // the next chunk's interval ends are loaded one chunk ahead, so their
+  // DRAM latency overlaps the current chunk's field evaluation
+  float n0a = 0.f, n1a = 0.f, n0b = 0.f, n1b = 0.f;
+  if (2 * lane < total) {
+    n0a = __ldg(t0 + wbeg + 2 * lane);
+    n1a = __ldg(t1 + wbeg + 2 * lane);
+  }
+  if (2 * lane + 1 < total) {
+    n0b = __ldg(t0 + wbeg + 2 * lane + 1);
+    n1b = __ldg(t1 + wbeg + 2 * lane + 1);
+  }
+  for (int base = 0; base < total; base += kChunk) {
+    const int nlive = min(kChunk, total - base);
+    Elem e[2];
+    e[0].a0 = n0a; e[0].a1 = n1a; e[1].a0 = n0b; e[1].a1 = n1b;
+    const int pa = base + kChunk + 2 * lane;
+    if (pa < total) {
+      n0a = __ldg(t0 + wbeg + pa);
+      n1a = __ldg(t1 + wbeg + pa);
+    }
+    if (pa + 1 < total) {
+      n0b = __ldg(t0 + wbeg + pa + 1);
+      n1b = __ldg(t1 + wbeg + pa + 1);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = base + 2 * lane + h;
+      const int own = (p >= s1) + (p >= s2) + (p >= s3);  // the last ray starting at or before p
+      e[h].own = own;
+      e[h].px = e[h].py = e[h].pz = 0.f;
+      if (p < total) {
+        const float4 A = rs[own][0], B = rs[own][1];
+        const float tm = 0.5f * (e[h].a0 + e[h].a1);
+        e[h].px = fmaf(tm, A.w, A.x);
+        e[h].py = fmaf(tm, B.x, A.y);
+        e[h].pz = fmaf(tm, B.y, A.z);
+      }
+    }
+    evals += composite_chunk2(fs, G, nlive, e[0], e[1], T_s, C_s);
+  }
+  if (has_ray) {
+    const float4 acc = C_s[lane];
+    reinterpret_cast<float4*>(rgba)[r] = make_float4(acc.x, acc.y, acc.z, 1.f - T_s[lane]);
+  }
+  if (count_evals && lane == 0) atomicAdd(&g_blob_evals, evals);
 }
 
 }  // namespace

@@ -7,21 +7,28 @@
 // the trained radiance field: sigma(x) = sum_g a_g exp(-|x - mu_g|^2 /
 // (2 s_g^2)), colour = the sigma-weighted mean of the blobs' colours.
 //
-// A warp works through its samples 32 at a time, one sample per lane, in ray
-// order.  A segmented warp scan (segments = rays) turns the per-sample
-// (1 - alpha) into transmittance inside the chunk; each ray's transmittance
-// so far and its colour sum are carried in shared memory (T_s, C_s, indexed
-// by the ray's slot in the warp) from chunk to chunk.
+// A warp works through its samples 64 at a time in ray order: lane l holds
+// the chunk's samples 2l and 2l + 1 ("elements" 0 and 1).  Every blob record
+// the warp reads from shared memory (a broadcast) thus serves two points, and
+// the two points are evaluated together with Blackwell's paired binary32
+// instructions (add/mul/fma .f32x2: one issue slot for both).  The shared
+// memory data path, not the arithmetic, limits a one-point-per-lane loop:
+// each broadcast record costs the same wavefronts whatever the lane uses it
+// for.  A segmented warp scan over the lanes' element pairs (segments = rays)
+// turns the per-sample (1 - alpha) into transmittance inside the chunk; each
+// ray's transmittance so far and its colour sum are carried in shared memory
+// (T_s, C_s, indexed by the ray's slot in the warp) from chunk to chunk.
 //
 // Blob culling: before evaluating a chunk, the warp takes the bounding box
-// of its 32 points and keeps, in a shared-memory list, only the blobs whose
-// centre lies within kCullSigmas standard deviations of that box.  A dropped
-// blob's weight at any of those points is below a * exp(-kCullSigmas^2 / 2)
-// = a * e^-24.5, about 2e-11 of its amplitude, far below the compositor's
-// 1e-5 tolerance.  Each kept blob costs one exp2 of fma(d^2, -log2(e) /
-// (2 s^2), log2(a)), so amplitudes must be non-negative.  Every product-sum
-// is written as an explicit fmaf, so the arithmetic does not depend on the
-// translation unit's contraction flags.
+// of its 64 points (six single-instruction warp reductions over binary32,
+// redux.sync.{min,max}.f32) and keeps, in a shared-memory list, only the
+// blobs whose centre lies within kCullSigmas standard deviations of that
+// box.  A dropped blob's weight at any of those points is below a *
+// exp(-kCullSigmas^2 / 2) = a * e^-24.5, about 2e-11 of its amplitude, far
+// below the compositor's 1e-5 tolerance.  Each kept blob costs one exp2 of
+// fma(d^2, -log2(e) / (2 s^2), log2(a)), so amplitudes must be non-negative.
+// Every product-sum is an explicit fused multiply-add, so the arithmetic
+// does not depend on the translation unit's contraction flags.
 #pragma once
 
 #include <cmath>
@@ -34,10 +41,12 @@ namespace {
 constexpr int kMaxGauss = 256;
 constexpr float kCullSigmas = 7.f;
 constexpr unsigned kFieldFull = 0xffffffffu;
+constexpr int kChunk = 64;  // samples per warp step: two per lane
 
-// One blob in shared memory, prescaled for exp2.
+// One blob in shared memory, prescaled for exp2; the centre is stored
+// negated so that x - mu is one add.
 struct BlobRec {
-  float4 pos;  // mu_x, mu_y, mu_z, -log2(e) / (2 s^2)
+  float4 pos;  // -mu_x, -mu_y, -mu_z, -log2(e) / (2 s^2)
   float4 col;  // log2(a), r, g, b
 };
 
@@ -66,7 +75,7 @@ __device__ __forceinline__ FieldSmem stage_blobs(unsigned char* smem, const floa
   for (int i = threadIdx.x; i < G; i += blockDim.x) {
     const float* f = field + 8 * i;
     const float s = f[3];
-    tab[i].pos = make_float4(f[0], f[1], f[2], -1.4426950408889634f / (2.f * s * s));
+    tab[i].pos = make_float4(-f[0], -f[1], -f[2], -1.4426950408889634f / (2.f * s * s));
     tab[i].col = make_float4(log2f(f[4]), f[5], f[6], f[7]);
     cut[i] = (kCullSigmas * s) * (kCullSigmas * s);
   }
@@ -79,128 +88,171 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Order-preserving float <-> uint32 keys, so that warp min/max reductions
-// run on the integer reduction unit.
-__device__ __forceinline__ uint32_t fkey(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u);
-}
-__device__ __forceinline__ float fkey_inv(uint32_t k) {
-  return __uint_as_float(k ^ (((k >> 31) - 1u) | 0x80000000u));
-}
+// Warp-wide minimum / maximum of binary32 values, one instruction each
+// (sm_100 and later).  NaN inputs are ignored.
 __device__ __forceinline__ float warp_min(float v) {
-  return fkey_inv(__reduce_min_sync(kFieldFull, fkey(v)));
+  float r;
+  asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
 }
 __device__ __forceinline__ float warp_max(float v) {
-  return fkey_inv(__reduce_max_sync(kFieldFull, fkey(v)));
+  float r;
+  asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
 }
 
-// One 32-sample chunk.  Lane `lane` holds a sample when `live`: the interval
-// [a0, a1) of the ray in slot `own`, evaluated at point (px, py, pz).  Live
-// lanes come first and are in ray order; `last` marks the lane holding the
-// warp's final sample.  Updates T_s[own] and C_s[own].  Returns the
-// chunk's blob evaluations (live samples x kept blobs), the same on every
-// lane.
-__device__ __forceinline__ int composite_chunk(const FieldSmem& fs, int G, bool live, bool last,
-                                               int own, float px, float py, float pz, float a0,
-                                               float a1, float* T_s, float4* C_s) {
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+
+// One sample of a chunk: the interval [a0, a1) of the ray in slot `own`,
+// evaluated at point (px, py, pz).
+struct Elem {
+  float px, py, pz, a0, a1;
+  int own;
+};
+
+// One 64-sample chunk.  Lane l holds the chunk's samples 2l (e0) and
+// 2l + 1 (e1); samples below `nlive` are live, the rest padding (live
+// samples come first and are in ray order, so a ray's samples are
+// consecutive).  Updates T_s[own] and C_s[own] of every ray the chunk
+// touches.  Returns the chunk's blob evaluations (live samples x kept
+// blobs), the same on every lane.
+__device__ __forceinline__ int composite_chunk2(const FieldSmem& fs, int G, int nlive,
+                                                const Elem& e0, const Elem& e1, float* T_s,
+                                                float4* C_s) {
   const int lane = threadIdx.x & 31;
-  float alpha = 0.f, wr = 0.f, wgr = 0.f, wb = 0.f;
-  int nevals;
+  const bool live0 = 2 * lane < nlive, live1 = 2 * lane + 1 < nlive;
+  float2 sig = splat(0.f), cr = sig, cg = sig, cb = sig;
+  int m = 0;
   {
     // bounding box of the chunk's points, then the blobs within reach of it
-    const float bx0 = warp_min(live ? px : INFINITY), by0 = warp_min(live ? py : INFINITY),
-                bz0 = warp_min(live ? pz : INFINITY);
-    const float bx1 = warp_max(live ? px : -INFINITY), by1 = warp_max(live ? py : -INFINITY),
-                bz1 = warp_max(live ? pz : -INFINITY);
+    const float bx0 = warp_min(fminf(live0 ? e0.px : INFINITY, live1 ? e1.px : INFINITY));
+    const float by0 = warp_min(fminf(live0 ? e0.py : INFINITY, live1 ? e1.py : INFINITY));
+    const float bz0 = warp_min(fminf(live0 ? e0.pz : INFINITY, live1 ? e1.pz : INFINITY));
+    const float bx1 = warp_max(fmaxf(live0 ? e0.px : -INFINITY, live1 ? e1.px : -INFINITY));
+    const float by1 = warp_max(fmaxf(live0 ? e0.py : -INFINITY, live1 ? e1.py : -INFINITY));
+    const float bz1 = warp_max(fmaxf(live0 ? e0.pz : -INFINITY, live1 ? e1.pz : -INFINITY));
     BlobRec* kept = fs.kept;
-    int m = 0;
     for (int q0 = 0; q0 < G; q0 += 32) {
       const int q = q0 + lane;
       bool near = false;
       BlobRec b;
       if (q < G) {
-        b = fs.tab[q];
-        const float ex = fmaxf(0.f, fmaxf(bx0 - b.pos.x, b.pos.x - bx1));
-        const float ey = fmaxf(0.f, fmaxf(by0 - b.pos.y, b.pos.y - by1));
-        const float ez = fmaxf(0.f, fmaxf(bz0 - b.pos.z, b.pos.z - bz1));
+        b = fs.tab[q];  // pos holds -mu
+        const float ex = fmaxf(0.f, fmaxf(bx0 + b.pos.x, -b.pos.x - bx1));
+        const float ey = fmaxf(0.f, fmaxf(by0 + b.pos.y, -b.pos.y - by1));
+        const float ez = fmaxf(0.f, fmaxf(bz0 + b.pos.z, -b.pos.z - bz1));
         near = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= fs.cut[q];
       }
       const unsigned ball = __ballot_sync(kFieldFull, near);
       if (near) kept[m + __popc(ball & ((1u << lane) - 1u))] = b;
       m += __popc(ball);
     }
-    nevals = m * __popc(__ballot_sync(kFieldFull, live));
     __syncwarp();
-    float sigma = 0.f, sr = 0.f, sg = 0.f, sbl = 0.f;
+    // both points of the lane at once: half x is e0, half y is e1
+    const float2 X = make_float2(e0.px, e1.px), Y = make_float2(e0.py, e1.py),
+                 Z = make_float2(e0.pz, e1.pz);
 #pragma unroll 4
     for (int i = 0; i < m; ++i) {
       const float4 P = kept[i].pos;
-      const float ex = px - P.x, ey = py - P.y, ez = pz - P.z;
-      const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
       const float4 C = kept[i].col;
-      const float w = ex2_approx(fmaf(d2, P.w, C.x));
-      sigma += w;
-      sr = fmaf(w, C.y, sr);
-      sg = fmaf(w, C.z, sg);
-      sbl = fmaf(w, C.w, sbl);
+      const float2 ex = __fadd2_rn(X, splat(P.x)), ey = __fadd2_rn(Y, splat(P.y)),
+                   ez = __fadd2_rn(Z, splat(P.z));
+      float2 d2 = __fmul2_rn(ez, ez);
+      d2 = __ffma2_rn(ey, ey, d2);
+      d2 = __ffma2_rn(ex, ex, d2);
+      const float2 a = __ffma2_rn(d2, splat(P.w), splat(C.x));
+      const float2 w = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+      sig = __fadd2_rn(sig, w);
+      cr = __ffma2_rn(w, splat(C.y), cr);
+      cg = __ffma2_rn(w, splat(C.z), cg);
+      cb = __ffma2_rn(w, splat(C.w), cb);
     }
     __syncwarp();
-    if (live) {
-      alpha = -expm1f(-sigma * (a1 - a0));
-      if (sigma > 0.f) {
-        const float inv = __fdividef(alpha, sigma);
-        wr = sr * inv;
-        wgr = sg * inv;
-        wb = sbl * inv;
-      }
+  }
+  // opacity and colour weight of each element
+  float alpha0 = 0.f, alpha1 = 0.f;
+  float3 w0 = make_float3(0.f, 0.f, 0.f), w1 = w0;
+  if (live0) {
+    alpha0 = -expm1f(-sig.x * (e0.a1 - e0.a0));
+    if (sig.x > 0.f) {
+      const float inv = __fdividef(alpha0, sig.x);
+      w0 = make_float3(cr.x * inv, cg.x * inv, cb.x * inv);
     }
   }
-  // segments = rays: each lane's segment starts at the last head at or below it
-  const int own_prev = __shfl_up_sync(kFieldFull, own, 1);
-  const int own_next = __shfl_down_sync(kFieldFull, own, 1);
-  const bool head = lane == 0 || own_prev != own;
-  const bool tail = live && (lane == 31 || own_next != own || last);
-  const unsigned heads = __ballot_sync(kFieldFull, head);
+  if (live1) {
+    alpha1 = -expm1f(-sig.y * (e1.a1 - e1.a0));
+    if (sig.y > 0.f) {
+      const float inv = __fdividef(alpha1, sig.y);
+      w1 = make_float3(cr.y * inv, cg.y * inv, cb.y * inv);
+    }
+  }
+  // Segments = rays.  e0 starts a segment when its ray differs from the
+  // previous lane's e1 (or at lane 0), e1 when its ray differs from e0.  The
+  // warp scans run over each lane's LAST segment (the one holding e1): its
+  // product of (1 - alpha) and its colour sum, restarting at every lane that
+  // holds a segment start.
+  const int own1_prev = __shfl_up_sync(kFieldFull, e1.own, 1);
+  const int own0_next = __shfl_down_sync(kFieldFull, e0.own, 1);
+  const bool head0 = lane == 0 || own1_prev != e0.own;
+  const bool head1 = e1.own != e0.own;
+  const float f0 = 1.f - alpha0, f1 = 1.f - alpha1;
+  const unsigned heads = __ballot_sync(kFieldFull, head0 || head1);
   const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
   bool in[5];
 #pragma unroll
   for (int b = 0; b < 5; ++b) in[b] = lane - (1 << b) >= start;
-  // transmittance through the segment (inclusive product of 1 - alpha)
-  float incl = 1.f - alpha;
+  // transmittance: inclusive product through e1 within its segment
+  float incl = head1 ? f1 : f0 * f1;
 #pragma unroll
   for (int b = 0; b < 5; ++b) {
     const float y = __shfl_up_sync(kFieldFull, incl, 1 << b);
     if (in[b]) incl *= y;
   }
-  float excl = __shfl_up_sync(kFieldFull, incl, 1);
-  if (head) excl = 1.f;
-  const float T0 = T_s[own];
-  const float Tj = T0 * excl;
-  float cr = Tj * wr, cg = Tj * wgr, cb = Tj * wb;
+  const float carry = __shfl_up_sync(kFieldFull, incl, 1);  // through the previous lane's e1
+  const float x0 = head0 ? 1.f : carry;                      // before e0, within its segment
+  const float x1 = head1 ? 1.f : x0 * f0;                    // before e1
+  const float T0b = T_s[e1.own];  // the ray's transmittance before this chunk
+  const float ta = T_s[e0.own] * x0, tb = T0b * x1;
+  const float3 c0 = make_float3(ta * w0.x, ta * w0.y, ta * w0.z);
+  const float3 c1 = make_float3(tb * w1.x, tb * w1.y, tb * w1.z);
+  float sr = head1 ? c1.x : c0.x + c1.x, sg = head1 ? c1.y : c0.y + c1.y,
+        sb = head1 ? c1.z : c0.z + c1.z;
 #pragma unroll
   for (int b = 0; b < 5; ++b) {
-    const float yr = __shfl_up_sync(kFieldFull, cr, 1 << b);
-    const float yg = __shfl_up_sync(kFieldFull, cg, 1 << b);
-    const float yb = __shfl_up_sync(kFieldFull, cb, 1 << b);
+    const float yr = __shfl_up_sync(kFieldFull, sr, 1 << b);
+    const float yg = __shfl_up_sync(kFieldFull, sg, 1 << b);
+    const float yb = __shfl_up_sync(kFieldFull, sb, 1 << b);
     if (in[b]) {
-      cr += yr;
-      cg += yg;
-      cb += yb;
+      sr += yr;
+      sg += yg;
+      sb += yb;
     }
   }
-  const float T_end = T0 * incl;
+  const float pr = __shfl_up_sync(kFieldFull, sr, 1), pg = __shfl_up_sync(kFieldFull, sg, 1),
+              pb = __shfl_up_sync(kFieldFull, sb, 1);
+  // e0 ends a segment when e1 is padding or starts another ray; e1 ends one
+  // at the lane's end when the next element is padding or another ray
+  const bool tail0 = live0 && (!live1 || head1);
+  const bool tail1 = live1 && (lane == 31 || 2 * lane + 2 >= nlive || own0_next != e1.own);
   __syncwarp();
-  if (tail) {
-    T_s[own] = T_end;
-    float4 acc = C_s[own];
-    acc.x += cr;
-    acc.y += cg;
-    acc.z += cb;
-    C_s[own] = acc;
+  if (tail0) {
+    T_s[e0.own] = ta * f0;
+    float4 acc = C_s[e0.own];
+    acc.x += (head0 ? 0.f : pr) + c0.x;
+    acc.y += (head0 ? 0.f : pg) + c0.y;
+    acc.z += (head0 ? 0.f : pb) + c0.z;
+    C_s[e0.own] = acc;
+  }
+  if (tail1) {
+    T_s[e1.own] = T0b * incl;
+    float4 acc = C_s[e1.own];
+    acc.x += sr;
+    acc.y += sg;
+    acc.z += sb;
+    C_s[e1.own] = acc;
   }
   __syncwarp();
-  return nevals;
+  return m * nlive;
 }
 
 }  // namespace

@@ -9,10 +9,11 @@
 // consecutive rays (measured faster than 4 or 16).  Every
 // lattice index k of a run is the sample (t_k, t_{k+1}) with midpoint tm_k,
 // read from the lattice table all rays share, so a warp numbers its rays'
-// samples locally (a warp scan of the run lengths), and lane j of each
-// 32-sample chunk finds its ray (binary search over the lanes' first
-// positions) and its run (binary search over that ray's runs in shared
-// memory).  No global scan, no sample arrays, no host read-back.
+// samples locally (a warp scan of the run lengths), and each sample of a
+// 64-sample chunk (two per lane, field.cuh) finds its ray (compares against
+// the slots' first positions, kept in registers) and its run (binary search
+// over that ray's runs in shared memory).  The task's rays are staged in
+// shared memory.  No global scan, no sample arrays, no host read-back.
 //
 // A ray with more than kMaxRuns runs is finished in rounds: after the runs
 // it has are composited, it walks again from the end of the last one
@@ -51,6 +52,18 @@ struct StoreArgs {
   unsigned* status;            // kDevCapacity when the samples do not fit
 };
 
+// Position p of a round (numbered over the warp's rays) -> its lattice index:
+// the run of slot `own` that starts at or before p.  Runs hold {first k,
+// first position}; unused slots have position kNoRun.
+__device__ __forceinline__ int run_k(const uint2* sr, int own, int p) {
+  int j = 0;
+#pragma unroll
+  for (int s = kMaxRuns / 2; s > 0; s >>= 1)
+    if (sr[(j + s) * kRenderRays + own].y <= (uint32_t)p) j += s;
+  const uint2 e = sr[j * kRenderRays + own];
+  return (int)e.x + (p - (int)e.y);
+}
+
 template <int kMode, bool kStore>
 __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
@@ -58,8 +71,10 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     const float* __restrict__ field, int G, float* __restrict__ rgba, bool count_evals,
     StoreArgs out) {
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kRenderWarps)
-  __shared__ float s_T[kRenderWarps][32];
-  __shared__ float4 s_C[kRenderWarps][32];
+  __shared__ float s_T[kRenderWarps][kRenderRays];
+  __shared__ float4 s_C[kRenderWarps][kRenderRays];
+  __shared__ float4 s_ray[kRenderWarps][kRenderRays][2];  // {o, d.x}, {d.y, d.z, -, -}
+  __shared__ int64_t s_gbase[kRenderWarps][kRenderRays];  // storing form: output of position 0
   // run j of ray slot i at [j * kRenderRays + i]: {first k, first position}
   __shared__ uint2 s_run[kRenderWarps][kMaxRuns * kRenderRays];
   const FieldSmem fs = stage_blobs(smem, field, G);
@@ -69,6 +84,8 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   if (task * kRenderRays >= n) return;  // uniform per warp; no block barrier follows
   float* T_s = s_T[wib];
   float4* C_s = s_C[wib];
+  float4 (*rs)[2] = s_ray[wib];
+  int64_t* gb = s_gbase[wib];
   uint2* sr = s_run[wib];
   unsigned long long evals = 0;  // this warp's blob evaluations
   const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
@@ -76,8 +93,12 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   const bool has_ray = lane < kRenderRays && r < n;
   Ray ray{};
   const bool ok = has_ray && load_ray(ro, rd, r, ray);
-  T_s[lane] = 1.f;
-  C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (lane < kRenderRays) {
+    T_s[lane] = 1.f;
+    C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    rs[lane][0] = make_float4(ray.o[0], ray.o[1], ray.o[2], ray.d[0]);
+    rs[lane][1] = make_float4(ray.d[1], ray.d[2], 0.f, 0.f);
+  }
   const int nr_all = ok ? (int)nruns[r] : 0;  // saturated at 255
   int nr = min(nr_all, kMaxRuns);
   for (int j = 0; j < nr; ++j) sr[j * kRenderRays + lane] = __ldg(runs + (int64_t)j * n + r);
@@ -85,7 +106,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   if (nr_all > kMaxRuns) k_next = (int)sr[(kMaxRuns - 1) * kRenderRays + lane].y;
   // storing form: lane i < kRenderRays holds ray i's CSR offset, then, per
   // round, the output position of the round's position 0 of that ray
-  int64_t gofs = 0, gbase = 0;
+  int64_t gofs = 0;
   if constexpr (kStore) {
     const int64_t tile = task >> 2;  // four 8-ray tasks per 32-ray tile
     const int64_t tr = tile * 32 + lane;
@@ -124,58 +145,55 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     }
     const int pos = inc - cnt;
     const int W = __shfl_sync(kFull, inc, 31);
-    if constexpr (kStore) gbase = gofs - pos;
+    // every lane keeps the first positions of slots 1 .. kRenderRays - 1
+    int q[kRenderRays];
+#pragma unroll
+    for (int i = 1; i < kRenderRays; ++i) q[i] = __shfl_sync(kFull, pos, i);
     if (lane < kRenderRays) {
-      int q = pos;
+      if constexpr (kStore) gb[lane] = gofs - pos;
+      int qq = pos;
       for (int j = 0; j < kMaxRuns; ++j) {
         uint2& e = sr[j * kRenderRays + lane];
         if (j < nr) {
           const int len = (int)(e.y - e.x);
-          e.y = (uint32_t)q;
-          q += len;
+          e.y = (uint32_t)qq;
+          qq += len;
         } else {
           e = make_uint2(0u, kNoRun);
         }
       }
     }
     __syncwarp();
-    for (int base = 0; base < W; base += 32) {
-      const int p = base + lane;
-      const bool live = p < W;
-      int own = 0;  // the last ray slot whose first position is <= p
+    for (int base = 0; base < W; base += kChunk) {
+      Elem e[2];
 #pragma unroll
-      for (int s = kRenderRays / 2; s > 0; s >>= 1) {
-        const int v = __shfl_sync(kFull, pos, own + s);
-        if (v <= p) own += s;
-      }
-      int j = 0;  // the last run of that ray starting at or before p
+      for (int hh = 0; hh < 2; ++hh) {
+        const int p = base + 2 * lane + hh;
+        int own = 0;  // the last slot whose first position is <= p
 #pragma unroll
-      for (int s = kMaxRuns / 2; s > 0; s >>= 1)
-        if (sr[(j + s) * kRenderRays + own].y <= (uint32_t)p) j += s;
-      const uint2 e = sr[j * kRenderRays + own];
-      const float ox = __shfl_sync(kFull, ray.o[0], own), oy = __shfl_sync(kFull, ray.o[1], own),
-                  oz = __shfl_sync(kFull, ray.o[2], own);
-      const float dx = __shfl_sync(kFull, ray.d[0], own), dy = __shfl_sync(kFull, ray.d[1], own),
-                  dz = __shfl_sync(kFull, ray.d[2], own);
-      float a0 = 0.f, a1 = 0.f, px = 0.f, py = 0.f, pz = 0.f;
-      if (live) {
-        const int k = (int)e.x + (p - (int)e.y);
-        a0 = __ldg(lat.t + k);
-        a1 = __ldg(lat.t + k + 1);
-        const float tm = __ldg(lat.tm + k);
-        px = fmaf(tm, dx, ox);
-        py = fmaf(tm, dy, oy);
-        pz = fmaf(tm, dz, oz);
-      }
-      if constexpr (kStore) {
-        const int64_t q = __shfl_sync(kFull, gbase, own) + p;
-        if (live && q < out.capacity) {
-          out.ray_idx[q] = (int32_t)(task * kRenderRays + own);
-          out.t0[q] = a0;
-          out.t1[q] = a1;
+        for (int i = 1; i < kRenderRays; ++i) own += p >= q[i];
+        e[hh].own = own;
+        e[hh].a0 = e[hh].a1 = e[hh].px = e[hh].py = e[hh].pz = 0.f;
+        if (p < W) {
+          const int k = run_k(sr, own, p);
+          e[hh].a0 = __ldg(lat.t + k);
+          e[hh].a1 = __ldg(lat.t + k + 1);
+          const float tm = __ldg(lat.tm + k);
+          const float4 A = rs[own][0], B = rs[own][1];
+          e[hh].px = fmaf(tm, A.w, A.x);
+          e[hh].py = fmaf(tm, B.x, A.y);
+          e[hh].pz = fmaf(tm, B.y, A.z);
+          if constexpr (kStore) {
+            const int64_t qo = gb[own] + p;
+            if (qo < out.capacity) {
+              out.ray_idx[qo] = (int32_t)(task * kRenderRays + own);
+              out.t0[qo] = e[hh].a0;
+              out.t1[qo] = e[hh].a1;
+            }
+          }
         }
       }
-      evals += composite_chunk(fs, G, live, p + 1 >= W, own, px, py, pz, a0, a1, T_s, C_s);
+      evals += composite_chunk2(fs, G, min(kChunk, W - base), e[0], e[1], T_s, C_s);
     }
     if constexpr (kStore) gofs += cnt;  // this round's samples of the lane's ray are written
     const bool more = k_next < lat.K;
