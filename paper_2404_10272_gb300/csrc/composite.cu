@@ -33,13 +33,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kWarpsPerCta)
   __shared__ float s_T[kWarpsPerCta][kRaysPerWarp];
   __shared__ float4 s_C[kWarpsPerCta][kRaysPerWarp];
-  __shared__ float4 s_ray[kWarpsPerCta][kRaysPerWarp][2];  // {o, d.x}, {d.y, d.z, -, -}
+  __shared__ float4 s_ray[kWarpsPerCta][kRaysPerWarp][2];  // {o, d.x}, {d.y, d.z, 1/|d|^2, -}
   const FieldSmem fs = stage_blobs(smem, field, G);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* T_s = s_T[wib];
   float4* C_s = s_C[wib];
-  float4 (*rs)[2] = s_ray[wib];
+  float4(*rs)[2] = s_ray[wib];
   unsigned long long evals = 0;  // this warp's blob evaluations
   const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (wg * kRaysPerWarp >= n) return;  // uniform per warp; no block barrier follows
@@ -57,8 +57,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
         d[c] = __ldg(rd + 3 * r + c);
       }
     }
+    const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
     rs[lane][0] = make_float4(o[0], o[1], o[2], d[0]);
-    rs[lane][1] = make_float4(d[1], d[2], 0.f, 0.f);
+    rs[lane][1] = make_float4(d[1], d[2], dd > 0.f ? 1.f / dd : 0.f, 0.f);
     T_s[lane] = 1.f;
     C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
         e[h].pz = fmaf(tm, B.y, A.z);
       }
     }
-    evals += composite_chunk2(fs, G, nlive, e[0], e[1], T_s, C_s);
+    evals += composite_chunk2(fs, G, nlive, e[0], e[1], rs, T_s, C_s);
   }
   if (has_ray) {
     const float4 acc = C_s[lane];

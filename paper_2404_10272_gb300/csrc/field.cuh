@@ -19,13 +19,17 @@
 // ray's transmittance so far and its colour sum are carried in shared memory
 // (T_s, C_s, indexed by the ray's slot in the warp) from chunk to chunk.
 //
-// Blob culling: before evaluating a chunk, the warp takes the bounding box
-// of its 64 points (six single-instruction warp reductions over binary32,
-// redux.sync.{min,max}.f32) and keeps, in a shared-memory list, only the
-// blobs whose centre lies within kCullSigmas standard deviations of that
-// box.  A dropped blob's weight at any of those points is below a *
-// exp(-kCullSigmas^2 / 2) = a * e^-24.5, about 2e-11 of its amplitude, far
-// below the compositor's 1e-5 tolerance.  Each kept blob costs one exp2 of
+// Blob culling: before evaluating a chunk, the warp keeps, in a shared-memory
+// list, only the blobs whose centre lies within kCullSigmas standard
+// deviations of the chunk's points: of the segments of the (one or two)
+// rays the points lie on, between the smallest and largest midpoint
+// parameter of each ray's samples in the chunk (single-instruction warp
+// reductions over binary32, redux.sync.{min,max}.f32), or of the points'
+// bounding box when the chunk spans three rays or more.  The reach carries a
+// relative margin of 1e-5 for binary32 rounding, so no blob within
+// kCullSigmas s of a point is dropped.  A dropped blob's weight at any of
+// those points is below a * exp(-kCullSigmas^2 / 2) = a * e^-24.5, about
+// 2e-11 of its amplitude, far below the compositor's 1e-5 tolerance.  Each kept blob costs one exp2 of
 // fma(d^2, -log2(e) / (2 s^2), log2(a)), so amplitudes must be non-negative.
 // Every product-sum is an explicit fused multiply-add, so the arithmetic
 // does not depend on the translation unit's contraction flags.
@@ -50,17 +54,23 @@ struct BlobRec {
   float4 col;  // log2(a), r, g, b
 };
 
+// The culling test's view of a blob: the negated centre and its reach,
+// kCullSigmas s plus a margin of 1e-5 |mu| (max norm) for binary32 rounding
+// in the distance tests.
+struct BlobCull {
+  float4 v;  // -mu_x, -mu_y, -mu_z, reach
+};
+
 // Dynamic shared memory of a compositing CTA with `warps` warps over G
-// blobs: the field (records, then (kCullSigmas s)^2 per blob), then one
-// list of kept records per warp.
+// blobs: the field records, their culling entries, then one list of kept
+// records per warp.
 __host__ __device__ inline size_t field_smem_bytes(int G, int warps) {
-  return (size_t)G * sizeof(BlobRec) + (((size_t)G * sizeof(float) + 15) & ~(size_t)15) +
-         (size_t)warps * G * sizeof(BlobRec);
+  return (size_t)G * (sizeof(BlobRec) + sizeof(BlobCull)) + (size_t)warps * G * sizeof(BlobRec);
 }
 
 struct FieldSmem {
   const BlobRec* tab;
-  const float* cut;
+  const BlobCull* cull;
   BlobRec* kept;  // this warp's list
 };
 
@@ -69,17 +79,17 @@ struct FieldSmem {
 __device__ __forceinline__ FieldSmem stage_blobs(unsigned char* smem, const float* __restrict__ field,
                                                  int G) {
   BlobRec* tab = reinterpret_cast<BlobRec*>(smem);
-  float* cut = reinterpret_cast<float*>(smem + (size_t)G * sizeof(BlobRec));
-  BlobRec* kept = reinterpret_cast<BlobRec*>(
-      smem + (size_t)G * sizeof(BlobRec) + (((size_t)G * sizeof(float) + 15) & ~(size_t)15));
+  BlobCull* cull = reinterpret_cast<BlobCull*>(smem + (size_t)G * sizeof(BlobRec));
+  BlobRec* kept = reinterpret_cast<BlobRec*>(smem + (size_t)G * (sizeof(BlobRec) + sizeof(BlobCull)));
   for (int i = threadIdx.x; i < G; i += blockDim.x) {
     const float* f = field + 8 * i;
     const float s = f[3];
     tab[i].pos = make_float4(-f[0], -f[1], -f[2], -1.4426950408889634f / (2.f * s * s));
     tab[i].col = make_float4(log2f(f[4]), f[5], f[6], f[7]);
-    cut[i] = (kCullSigmas * s) * (kCullSigmas * s);
+    const float mu_max = fmaxf(fabsf(f[0]), fmaxf(fabsf(f[1]), fabsf(f[2])));
+    cull[i].v = make_float4(-f[0], -f[1], -f[2], kCullSigmas * s + 1e-5f * mu_max);
   }
-  return FieldSmem{tab, cut, kept + (threadIdx.x >> 5) * G};
+  return FieldSmem{tab, cull, kept + (threadIdx.x >> 5) * G};
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -103,6 +113,43 @@ __device__ __forceinline__ float warp_max(float v) {
 
 __device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
 
+// The part of one ray that a chunk's samples of it lie on: centre point c,
+// half-length hh in the ray's parameter, direction d and 1 / |d|^2.
+struct Segment {
+  float cx, cy, cz, hh, dx, dy, dz, idd;
+};
+
+// Squared distance from the blob centre (given negated) to the segment.
+__device__ __forceinline__ float seg_dist2(const Segment& S, const float4& nmu) {
+  const float wx = S.cx + nmu.x, wy = S.cy + nmu.y, wz = S.cz + nmu.z;  // c - mu
+  const float u = -fmaf(wx, S.dx, fmaf(wy, S.dy, wz * S.dz)) * S.idd;
+  const float t = fminf(fmaxf(u, -S.hh), S.hh);
+  const float qx = fmaf(t, S.dx, wx), qy = fmaf(t, S.dy, wy), qz = fmaf(t, S.dz, wz);
+  return fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+}
+
+// Segment of ray slot `slot` over the parameter range [tmin, tmax] (midpoint
+// parameters of its samples in the chunk); rs[slot] = {o, d.x}, {d.y, d.z,
+// 1/|d|^2, -}.  Also returns the rounding margin for distances to it.
+__device__ __forceinline__ Segment make_segment(const float4 (*rs)[2], int slot, float tmin,
+                                                float tmax, float& eps) {
+  const float4 A = rs[slot][0], B = rs[slot][1];
+  const float tmid = 0.5f * (tmin + tmax);
+  Segment S;
+  S.hh = 0.5f * (tmax - tmin);
+  S.dx = A.w;
+  S.dy = B.x;
+  S.dz = B.y;
+  S.idd = B.z;
+  S.cx = fmaf(tmid, S.dx, A.x);
+  S.cy = fmaf(tmid, S.dy, A.y);
+  S.cz = fmaf(tmid, S.dz, A.z);
+  const float cm = fmaxf(fabsf(S.cx), fmaxf(fabsf(S.cy), fabsf(S.cz)));
+  const float dm = fmaxf(fabsf(S.dx), fmaxf(fabsf(S.dy), fabsf(S.dz)));
+  eps = 1e-5f * (1.f + cm + S.hh * dm);
+  return S;
+}
+
 // One sample of a chunk: the interval [a0, a1) of the ray in slot `own`,
 // evaluated at point (px, py, pz).
 struct Elem {
@@ -117,34 +164,68 @@ struct Elem {
 // touches.  Returns the chunk's blob evaluations (live samples x kept
 // blobs), the same on every lane.
 __device__ __forceinline__ int composite_chunk2(const FieldSmem& fs, int G, int nlive,
-                                                const Elem& e0, const Elem& e1, float* T_s,
+                                                const Elem& e0, const Elem& e1,
+                                                const float4 (*rs)[2], float* T_s,
                                                 float4* C_s) {
   const int lane = threadIdx.x & 31;
   const bool live0 = 2 * lane < nlive, live1 = 2 * lane + 1 < nlive;
   float2 sig = splat(0.f), cr = sig, cg = sig, cb = sig;
   int m = 0;
   {
-    // bounding box of the chunk's points, then the blobs within reach of it
-    const float bx0 = warp_min(fminf(live0 ? e0.px : INFINITY, live1 ? e1.px : INFINITY));
-    const float by0 = warp_min(fminf(live0 ? e0.py : INFINITY, live1 ? e1.py : INFINITY));
-    const float bz0 = warp_min(fminf(live0 ? e0.pz : INFINITY, live1 ? e1.pz : INFINITY));
-    const float bx1 = warp_max(fmaxf(live0 ? e0.px : -INFINITY, live1 ? e1.px : -INFINITY));
-    const float by1 = warp_max(fmaxf(live0 ? e0.py : -INFINITY, live1 ? e1.py : -INFINITY));
-    const float bz1 = warp_max(fmaxf(live0 ? e0.pz : -INFINITY, live1 ? e1.pz : -INFINITY));
+    // The blobs within reach of the chunk's points.  A chunk holds the
+    // samples of one or two rays (its first and last ray slot) in most
+    // cases: the points of a ray lie on a segment of it, so a blob is kept
+    // when it lies within reach of one of those segments.  With three rays
+    // or more, the test is against the points' bounding box.
+    const int s_first = __shfl_sync(kFieldFull, e0.own, 0);
+    const int s_last =
+        (int)__reduce_max_sync(kFieldFull, (unsigned)(live1 ? e1.own : live0 ? e0.own : 0));
+    const bool segs = s_last - s_first <= 1, two = s_last != s_first;
+    Segment SA, SB;
+    float epsA = 0.f, epsB = 0.f;
+    float bx0 = 0.f, by0 = 0.f, bz0 = 0.f, bx1 = 0.f, by1 = 0.f, bz1 = 0.f;
+    if (segs) {
+      const float tm0 = 0.5f * (e0.a0 + e0.a1), tm1 = 0.5f * (e1.a0 + e1.a1);
+      const bool a0 = live0 && e0.own == s_first, a1 = live1 && e1.own == s_first;
+      const float tA0 = warp_min(fminf(a0 ? tm0 : INFINITY, a1 ? tm1 : INFINITY));
+      const float tA1 = warp_max(fmaxf(a0 ? tm0 : -INFINITY, a1 ? tm1 : -INFINITY));
+      SA = make_segment(rs, s_first, tA0, tA1, epsA);
+      if (two) {
+        const bool b0 = live0 && e0.own == s_last, b1 = live1 && e1.own == s_last;
+        const float tB0 = warp_min(fminf(b0 ? tm0 : INFINITY, b1 ? tm1 : INFINITY));
+        const float tB1 = warp_max(fmaxf(b0 ? tm0 : -INFINITY, b1 ? tm1 : -INFINITY));
+        SB = make_segment(rs, s_last, tB0, tB1, epsB);
+      }
+    } else {
+      bx0 = warp_min(fminf(live0 ? e0.px : INFINITY, live1 ? e1.px : INFINITY));
+      by0 = warp_min(fminf(live0 ? e0.py : INFINITY, live1 ? e1.py : INFINITY));
+      bz0 = warp_min(fminf(live0 ? e0.pz : INFINITY, live1 ? e1.pz : INFINITY));
+      bx1 = warp_max(fmaxf(live0 ? e0.px : -INFINITY, live1 ? e1.px : -INFINITY));
+      by1 = warp_max(fmaxf(live0 ? e0.py : -INFINITY, live1 ? e1.py : -INFINITY));
+      bz1 = warp_max(fmaxf(live0 ? e0.pz : -INFINITY, live1 ? e1.pz : -INFINITY));
+    }
     BlobRec* kept = fs.kept;
     for (int q0 = 0; q0 < G; q0 += 32) {
       const int q = q0 + lane;
       bool near = false;
-      BlobRec b;
       if (q < G) {
-        b = fs.tab[q];  // pos holds -mu
-        const float ex = fmaxf(0.f, fmaxf(bx0 + b.pos.x, -b.pos.x - bx1));
-        const float ey = fmaxf(0.f, fmaxf(by0 + b.pos.y, -b.pos.y - by1));
-        const float ez = fmaxf(0.f, fmaxf(bz0 + b.pos.z, -b.pos.z - bz1));
-        near = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= fs.cut[q];
+        const float4 c = fs.cull[q].v;  // -mu, reach
+        if (segs) {
+          const float ra = c.w + epsA;
+          near = seg_dist2(SA, c) <= ra * ra;
+          if (two) {  // warp-uniform
+            const float rb = c.w + epsB;
+            near |= seg_dist2(SB, c) <= rb * rb;
+          }
+        } else {
+          const float ex = fmaxf(0.f, fmaxf(bx0 + c.x, -c.x - bx1));
+          const float ey = fmaxf(0.f, fmaxf(by0 + c.y, -c.y - by1));
+          const float ez = fmaxf(0.f, fmaxf(bz0 + c.z, -c.z - bz1));
+          near = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= c.w * c.w;
+        }
       }
       const unsigned ball = __ballot_sync(kFieldFull, near);
-      if (near) kept[m + __popc(ball & ((1u << lane) - 1u))] = b;
+      if (near) kept[m + __popc(ball & ((1u << lane) - 1u))] = fs.tab[q];
       m += __popc(ball);
     }
     __syncwarp();

@@ -53,10 +53,10 @@ struct StoreArgs {
 };
 
 // Position p of a round (numbered over the warp's rays) -> its lattice index:
-// the run of slot `own` that starts at or before p.  Runs hold {first k,
+// the run j of slot `own` that starts at or before p.  Runs hold {first k,
 // first position}; unused slots have position kNoRun.
-__device__ __forceinline__ int run_k(const uint2* sr, int own, int p) {
-  int j = 0;
+__device__ __forceinline__ int run_k(const uint2* sr, int own, int p, int& j) {
+  j = 0;
 #pragma unroll
   for (int s = kMaxRuns / 2; s > 0; s >>= 1)
     if (sr[(j + s) * kRenderRays + own].y <= (uint32_t)p) j += s;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kRenderWarps)
   __shared__ float s_T[kRenderWarps][kRenderRays];
   __shared__ float4 s_C[kRenderWarps][kRenderRays];
-  __shared__ float4 s_ray[kRenderWarps][kRenderRays][2];  // {o, d.x}, {d.y, d.z, -, -}
+  __shared__ float4 s_ray[kRenderWarps][kRenderRays][2];  // {o, d.x}, {d.y, d.z, 1/|d|^2, -}
   __shared__ int64_t s_gbase[kRenderWarps][kRenderRays];  // storing form: output of position 0
   // run j of ray slot i at [j * kRenderRays + i]: {first k, first position}
   __shared__ uint2 s_run[kRenderWarps][kMaxRuns * kRenderRays];
@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   if (lane < kRenderRays) {
     T_s[lane] = 1.f;
     C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float dd = fmaf(ray.d[0], ray.d[0], fmaf(ray.d[1], ray.d[1], ray.d[2] * ray.d[2]));
     rs[lane][0] = make_float4(ray.o[0], ray.o[1], ray.o[2], ray.d[0]);
-    rs[lane][1] = make_float4(ray.d[1], ray.d[2], 0.f, 0.f);
+    rs[lane][1] = make_float4(ray.d[1], ray.d[2], dd > 0.f ? 1.f / dd : 0.f, 0.f);
   }
   const int nr_all = ok ? (int)nruns[r] : 0;  // saturated at 255
   int nr = min(nr_all, kMaxRuns);
@@ -108,7 +109,8 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   // round, the output position of the round's position 0 of that ray
   int64_t gofs = 0;
   if constexpr (kStore) {
-    const int64_t tile = task >> 2;  // four 8-ray tasks per 32-ray tile
+    constexpr int kTasksPerTile = 32 / kRenderRays;
+    const int64_t tile = task / kTasksPerTile;
     const int64_t tr = tile * 32 + lane;
     const int64_t c = tr < n ? (int64_t)__ldg(out.counts + tr) : 0;
     int64_t inc = c;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
       if (lane >= o) inc += y;
     }
     const int64_t ex = __ldg(out.tile_prefix + tile) + inc - c;
-    const int first = (int)(task & 3) * kRenderRays;
+    const int first = (int)(task % kTasksPerTile) * kRenderRays;
     gofs = __shfl_sync(kFull, ex, first + (lane & (kRenderRays - 1)));
     const int64_t mine = __shfl_sync(kFull, c, first + (lane & (kRenderRays - 1)));
     // capacity 0 counts only: offsets unclamped, no samples, no status
@@ -166,6 +168,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     __syncwarp();
     for (int base = 0; base < W; base += kChunk) {
       Elem e[2];
+      int k0 = 0, j0 = 0;
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         const int p = base + 2 * lane + hh;
@@ -175,10 +178,22 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
         e[hh].own = own;
         e[hh].a0 = e[hh].a1 = e[hh].px = e[hh].py = e[hh].pz = 0.f;
         if (p < W) {
-          const int k = run_k(sr, own, p);
-          e[hh].a0 = __ldg(lat.t + k);
+          int k;
+          if (hh == 1 && own == e[0].own &&
+              (j0 + 1 >= kMaxRuns || (uint32_t)p < sr[(j0 + 1) * kRenderRays + own].y)) {
+            // the next lattice index of e0's run: its start is e0's end
+            k = k0 + 1;
+            e[1].a0 = e[0].a1;
+          } else {
+            int j;
+            k = run_k(sr, own, p, j);
+            e[hh].a0 = __ldg(lat.t + k);
+            k0 = k;
+            j0 = j;
+          }
           e[hh].a1 = __ldg(lat.t + k + 1);
-          const float tm = __ldg(lat.tm + k);
+          // the midpoint as the lattice defines it: fl(fl(t_k + t_k+1) * 0.5)
+          const float tm = __fmul_rn(__fadd_rn(e[hh].a0, e[hh].a1), 0.5f);
           const float4 A = rs[own][0], B = rs[own][1];
           e[hh].px = fmaf(tm, A.w, A.x);
           e[hh].py = fmaf(tm, B.x, A.y);
@@ -193,7 +208,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
           }
         }
       }
-      evals += composite_chunk2(fs, G, min(kChunk, W - base), e[0], e[1], T_s, C_s);
+      evals += composite_chunk2(fs, G, min(kChunk, W - base), e[0], e[1], rs, T_s, C_s);
     }
     if constexpr (kStore) gofs += cnt;  // this round's samples of the lane's ray are written
     const bool more = k_next < lat.K;
