@@ -2,18 +2,23 @@
 """Benchmark of the occupancy-grid ray sampler on one GB300 (or N, as
 independent replicas of the per-frame work).
 
-One step = one frame of the object-centric workload (one 128^3 level over
-[-1.5, 1.5)^3, 800x800 rays from one of 20 seeded cameras, step
-fl32(sqrt(3)*3/1024), near 2, far 6): rebuild the VDB grid from the dense
-occupancy, hierarchical-DDA sampling (count, scan, emit), and compositing
-over the 64-blob field.  Rays of all 20 cameras stay resident in HBM; the L2
-is flushed between timed steps (the flush is outside the timed windows).
+One step = one frame of the unbounded workload, the largest single-GPU frame
+(a cascade of four 128^3 levels, level l over [-2^l, 2^l)^3, 1245x825 rays
+from one of 20 seeded cameras inside the inner box, near 0.02, far 1e3, step
+1.73e-3, cone 0.004): rebuild the VDB grid from the dense occupancy,
+hierarchical-DDA sampling (count, scan, emit), and compositing over the
+64-blob field.  Rays of all 20 cameras stay resident in HBM; the L2 is
+flushed between timed steps (the flush is outside the timed windows).
 
 Prints one JSON line (rank 0).  `value` is rays/s of the whole step; the
 line also carries the sampler alone for HDDA and for the dense-DDA
 baseline (rays/s, samples/s), per-kernel times, the roofline of the
-dominant kernel, the end-to-end rate through the public API with host
-buffers, and the CPU oracle's rate on a bounded sample of the same work.
+dominant kernel and of the sampler, the end-to-end rate through the public
+API with host buffers, and the CPU oracle's rate on a bounded sample of the
+same work.  A default single-GPU run adds three summaries: the
+object-centric frame (one 128^3 level, 800x800 rays) under `object`, the
+batched sampler under `batch`, and the server's p50/p99 latency at a fixed
+offered load under `serve`.
 
 --impl reference times the CPU oracle (binary32 brute-force sampler plus
 binary64 compositor) on bounded samples of the same workload.
@@ -35,12 +40,13 @@ if ROOT not in sys.path:
 
 N_CAMERAS = 20
 L2_FLUSH_BYTES = 256 << 20
-# FP32-pipe instructions per evaluated blob in the compositor: 3 sub, 1 mul + 2 fma
-# (squared distance), 1 fma (scaled exponent plus log2 amplitude), 1 add (density),
-# 3 fma (colour); the exp2 runs on the MUFU pipe alongside.  The compositor skips
-# blobs beyond 7 s of a chunk by definition; the library counts the evaluations it
-# does make when its work counters are on ("composite_blob_evals"), which the bench
-# does in a separate untimed pass.
+# FP32 operations per evaluated blob in the compositor: 3 sub, 1 mul + 2 fma (squared
+# distance), 1 fma (scaled exponent plus log2 amplitude), 1 add (density), 3 fma (colour);
+# the exp2 runs on the MUFU pipe alongside.  The compositor evaluates two samples per
+# lane with paired (f32x2) instructions, so this is 5.5 instructions per evaluation.  It
+# skips blobs beyond 7 s of a chunk's points by definition; the library counts the
+# evaluations it does make when its work counters are on ("composite_blob_evals"), which
+# the bench does in a separate untimed pass.
 COMPOSITE_FP32_PER_BLOB = 11
 KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # L2 hit rate and warp execution efficiency (active lanes per warp instruction) per kernel
@@ -48,17 +54,15 @@ KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # when a kernel changes.
 PROFILED_COUNTERS = {
     "object": {"hdda_walk": {"l2_hit_pct": 37.6, "active_lanes_of_32": 24.59},
-               "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98},
-               "composite": {"l2_hit_pct": 36.5, "active_lanes_of_32": 31.92}},
+               "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98}},
 }
-# DRAM bytes (read + write) per launch from ncu --set full of a workload's step on
-# camera 0 (the capture commands are kept with the profile summaries), for the
-# roofline's "traffic"; an entry must be dropped whenever its kernel changes, and a
-# workload without a capture reports none.
+# DRAM bytes (read + write) per launch from ncu of a workload's step on camera 0 (the
+# capture commands are kept with the profile summaries), for the roofline's "traffic"; an
+# entry must be dropped whenever its kernel changes, and a workload without a capture
+# reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 237_030_400, "hdda_emit": 269_582_080, "hdda_walk": 15_695_104},
-    "unbounded": {"composite": 1_502_856_960, "hdda_emit": 2_182_746_624,
-                  "hdda_walk": 26_170_880},
+    "object": {"hdda_emit": 269_582_080, "hdda_walk": 15_695_104},
+    "unbounded": {"hdda_emit": 2_182_746_624, "hdda_walk": 26_170_880},
 }
 
 
@@ -69,14 +73,17 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline workload only: no object-centric, batch or serve summaries")
     ap.add_argument("--cpu-stride", type=int, default=None,
                     help="CPU baseline sample: every n-th ray of camera 0 (default per workload)")
     ap.add_argument("--workload", choices=["object", "unbounded", "tiny", "batch", "serve"],
-                    default="object",
-                    help="object / unbounded / tiny: the per-frame step on that scene (object is "
-                         "the default line); batch: 64 mixed jobs in one graph launch against 64 "
-                         "separate launches; serve: continuous-batching render server under "
-                         "Poisson load")
+                    default="unbounded",
+                    help="unbounded / object / tiny: the per-frame step on that scene (unbounded, "
+                         "the largest single-GPU frame, is the default line and carries the "
+                         "object-centric, batch and serve summaries); batch: 64 mixed jobs in one "
+                         "graph launch against 64 separate launches; serve: continuous-batching "
+                         "render server under Poisson load")
     ap.add_argument("--profile-step", choices=["hdda", "dense", "render"], default=None,
                     help="profiling aid: one count-only call, one warm-up step and one step of "
                          "the given path on camera 0, no timing, no JSON line")
@@ -170,7 +177,9 @@ def frame_workload(name: str):
 # ---------------------------------------------------------------------------
 
 def run_ours(args):
-    import numpy as np
+    """The headline line: the per-frame step on the chosen workload (the unbounded one by
+    default), with the object-centric frame, the batched sampler and the server's latency
+    summarised beside it on a default single-GPU run."""
     import torch
     import torch.distributed as dist
 
@@ -182,9 +191,44 @@ def run_ours(args):
         dist.init_process_group("gloo")
     import __graft_entry__
     __graft_entry__.build()
+    line = measure_frame(args, args.workload, full=True)
+    if world == 1 and not args.no_extras and args.workload == "unbounded":
+        obj = measure_frame(args, "object", full=False)
+        line["object"] = object_summary(obj)
+        line["batch"] = run_batch(args, quick=True)
+        line["serve"] = run_serve(args, quick=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def object_summary(d: dict) -> dict:
+    """The object-centric frame's figures for the headline line's `object` key."""
+    keep = ("ms_per_step", "value", "samples_per_step", "hdda_sampler", "dense_dda_sampler",
+            "hdda_vs_dense_sampler_speedup", "roofline", "roofline_sampler", "render_only_step",
+            "dense_dda_step", "grid", "candidates_per_ray")
+    out = {"workload": d["config"]["workload"], "rays_per_step": d["config"]["rays_per_step"],
+           "steps": d["steps"], "rays_per_s": d["value"]}
+    out.update({k: d[k] for k in keep if k in d and k != "value"})
+    out["kernels"] = {k: v["avg_ms"] for k, v in d["kernels"].items()}
+    out["render_only_step"] = {k: v for k, v in d["render_only_step"].items()
+                               if k in ("rays_per_s", "ms_per_step", "vs_step")}
+    return out
+
+
+def measure_frame(args, workload: str, full: bool = True) -> dict:
+    """All figures of one per-frame workload.  full=False keeps the step, both samplers,
+    the dense-DDA and render-only steps and the rooflines (a summary block); full=True adds
+    the remaining variants, the incremental rebuild, the end-to-end loop and the CPU
+    baselines."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
     from paper_2404_10272_gb300 import hdda, replicas, scenes
 
-    sc, cams, desc, stride = frame_workload(args.workload)
+    rank, world, local = dist_env()
+    sc, cams, desc, stride = frame_workload(workload)
     rays = [c.rays() for c in cams]
     n = rays[0][0].shape[0]
     O = torch.stack([torch.from_numpy(o) for o, _ in rays]).cuda()
@@ -320,15 +364,19 @@ def run_ours(args):
     # breakdown comes from a second, profiled pass over the same steps
     ms, samples, _, _ = timed(step_hdda, K, W)
     ms_prof, _, kern, _ = timed(step_hdda, K, 2, profile=True)
-    ms_sync, _, _, _ = timed(step_hdda_sync, max(3, K // 2), 2)
-    ms_dense, samples_dense, kern_dense, _ = timed(step_dense, max(3, K // 2), 2, profile=True)
+    K2 = max(3, K // 2)
+    ms_dense, samples_dense, kern_dense, _ = timed(step_dense, K2, 2, profile=True)
     ms_sh, samp_sh, _, _ = timed(sampler_hdda, K, 2)
-    ms_sd, samp_sd, _, _ = timed(sampler_dense, max(3, K // 2), 2)
-    ms_sp, samp_sp, _, _ = timed(sampler_hdda_plain, max(3, K // 2), 2)
-    ms_ss, _, _, _ = timed(sampler_hdda_skip, max(3, K // 2), 2)
-    ms_ds, _, _, _ = timed(sampler_dense_skip, max(3, K // 2), 2)
+    ms_sd, samp_sd, _, _ = timed(sampler_dense, K2, 2)
     ms_r, _, kern_r, _ = timed(render_step, K, 2, profile=True)
-    ms_f, _, kern_f, _ = timed(fused_step, K, 2, profile=True)
+    ms_sync = ms_sp = ms_ss = ms_ds = ms_f = None
+    kern_f = {}
+    if full:
+        ms_sync, _, _, _ = timed(step_hdda_sync, K2, 2)
+        ms_sp, samp_sp, _, _ = timed(sampler_hdda_plain, K2, 2)
+        ms_ss, _, _, _ = timed(sampler_hdda_skip, K2, 2)
+        ms_ds, _, _, _ = timed(sampler_dense_skip, K2, 2)
+        ms_f, _, kern_f, _ = timed(fused_step, K, 2, profile=True)
 
     # incremental rebuild: 1 % of the 8^3 blocks change (one voxel each, in partial
     # blocks, so the leaves are rewritten in place) and again 1 % with a new leaf each
@@ -382,18 +430,21 @@ def run_ours(args):
 
     if int(tstatus.item()) != 0:
         raise RuntimeError(f"hdda_traverse_async raised device status {int(tstatus.item())}")
-    upd = {"object_grid": update_bench(sc.occ, sc.aabbs)}
-    # a large cascade (2 x 512^3, 256 MiB of voxels): the update reads only the listed blocks
-    big_rng = np.random.default_rng(78)
-    big = np.zeros((2, 512, 512, 512), np.uint8)
-    big.reshape(-1)[big_rng.integers(0, big.size, size=big.size // 500)] = 1
-    for l in range(2):
-        for _ in range(40):
-            a0 = big_rng.integers(0, 448, size=3)
-            b0 = a0 + big_rng.integers(8, 64, size=3)
-            big[l, a0[0]:b0[0], a0[1]:b0[1], a0[2]:b0[2]] = 1
-    upd["2x512_grid"] = update_bench(big, scenes.cascade_boxes(2, 1.0))
-    del big
+    upd = None
+    if full:
+        upd = {"this_grid": update_bench(sc.occ, sc.aabbs)}
+        # a large cascade (2 x 512^3, 256 MiB of voxels): the update reads only the listed
+        # blocks
+        big_rng = np.random.default_rng(78)
+        big = np.zeros((2, 512, 512, 512), np.uint8)
+        big.reshape(-1)[big_rng.integers(0, big.size, size=big.size // 500)] = 1
+        for l in range(2):
+            for _ in range(40):
+                a0 = big_rng.integers(0, 448, size=3)
+                b0 = a0 + big_rng.integers(8, 64, size=3)
+                big[l, a0[0]:b0[0], a0[1]:b0[1], a0[2]:b0[2]] = 1
+        upd["2x512_grid"] = update_bench(big, scenes.cascade_boxes(2, 1.0))
+        del big
     clk = clocks.stop()
     if int(status.item()) != 0:
         raise RuntimeError(f"hdda_render raised device status {int(status.item())}")
@@ -422,7 +473,7 @@ def run_ours(args):
     # travel while step j computes and step j's frame returns while step j+1
     # computes; events keep each slot's buffers from being reused early.
     e2e = None
-    if world >= 1:
+    if full:
         o_host = [torch.from_numpy(o).pin_memory() for o, _ in rays]
         d_host = [torch.from_numpy(d).pin_memory() for _, d in rays]
         out_host = [torch.empty((n, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
@@ -512,7 +563,7 @@ def run_ours(args):
         "composite": 24 * n + 8 * (n + 1) + 8 * S_avg + 16 * n + 32 * G,
     }
     alg_inst = {"composite": evals_step * COMPOSITE_FP32_PER_BLOB}
-    traffic = PROFILED_TRAFFIC.get(args.workload, {})
+    traffic = PROFILED_TRAFFIC.get(workload, {})
     per_kernel = {}
     for name, (launches, tot_ms) in kern.items():
         avg = tot_ms / max(1, launches)
@@ -522,9 +573,9 @@ def run_ours(args):
             ent["gbs"] = round(alg_bytes[name] / (avg / 1e3) / 1e9, 1)
         if name in traffic:
             ent["traffic"] = traffic[name]
-        ent.update(PROFILED_COUNTERS.get(args.workload, {}).get(name, {}))
+        ent.update(PROFILED_COUNTERS.get(workload, {}).get(name, {}))
         if name in alg_inst:
-            ent["tinst_s"] = round(alg_inst[name] / (avg / 1e3) / 1e12, 2)
+            ent["fp32_tops"] = round(alg_inst[name] / (avg / 1e3) / 1e12, 2)
             ent["blob_evals_per_sample"] = round(evals_step / max(S_avg, 1), 2)
         per_kernel[name] = ent
 
@@ -534,7 +585,7 @@ def run_ours(args):
         if name in alg_inst:
             ach = alg_inst[name] / (avg / 1e3) / 1e12
             return {"kernel": name, "bound": "alu", "achieved": round(ach, 2),
-                    "peak": round(alu_peak, 2), "unit": "Tinst/s (FP32 pipe)",
+                    "peak": round(alu_peak, 2), "unit": "T FP32 ops/s",
                     "frac": round(ach / alu_peak, 4), "traffic": traffic.get(name),
                     "alg_bytes": int(alg_bytes.get(name, 0)),
                     "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock"}
@@ -563,7 +614,7 @@ def run_ours(args):
 
     # --- CPU oracle on a bounded sample (rank 0, N = 1) -------------------
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if full and rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, rays[0], args.cpu_stride or stride)
         cpu["all_cores"] = cpu_baseline_all_cores(sc, rays[0],
                                                   max(1, (args.cpu_stride or stride) // 4))
@@ -595,34 +646,13 @@ def run_ours(args):
                          "samples_per_s": round(samp_sh * world / (ms_sh / 1e3), 1),
                          "candidates_per_s": round(n * K_cand * K * world / (ms_sh / 1e3), 1),
                          "ms_per_frame": round(ms_sh / K, 4)},
-        "dense_dda_sampler": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_sd / 1e3), 1),
+        "dense_dda_sampler": {"rays_per_s": round(n * K2 * world / (ms_sd / 1e3), 1),
                               "samples_per_s": round(samp_sd * world / (ms_sd / 1e3), 1),
-                              "candidates_per_s": round(n * K_cand * max(3, K // 2) * world
+                              "candidates_per_s": round(n * K_cand * K2 * world
                                                         / (ms_sd / 1e3), 1),
-                              "ms_per_frame": round(ms_sd / max(3, K // 2), 4)},
-        "hdda_plain_vdb_sampler": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_sp / 1e3), 1),
-                                   "ms_per_frame": round(ms_sp / max(3, K // 2), 4),
-                                   "note": "HDDA on the plain VDB tree (8^3 leaves, 16^3-block "
-                                           "nodes), refinement masks off"},
-        "skip_form_samplers": {
-            "note": "Algorithm 2 control flow (leading empty regions in an inner loop); same samples",
-            "hdda_ms_per_frame": round(ms_ss / max(3, K // 2), 4),
-            "dense_ms_per_frame": round(ms_ds / max(3, K // 2), 4)},
-        "dense_dda_step": {"rays_per_s": round(n * max(3, K // 2) * world / (ms_dense / 1e3), 1),
-                           "ms_per_step": round(ms_dense / max(3, K // 2), 4)},
-        "synchronous_step": {"note": "the same step through hdda_traverse_hdda, which reads the "
-                                     "sample total back to the host before compositing",
-                             "ms_per_step": round(ms_sync / max(3, K // 2), 4)},
-        "incremental_update": upd,
-        "fused_step": {
-            "note": "vdb rebuild + hdda_traverse_composite: the walk and the tile scan, then one "
-                    "kernel that writes every sample at its CSR position and composites it (the "
-                    "same samples as the step, the render-only path's frame)",
-            "rays_per_s": round(n * K * world / (ms_f / 1e3), 1),
-            "ms_per_step": round(ms_f / K, 4),
-            "vs_step": round(ms / ms_f, 3),
-            "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}
-                        for k, v in kern_f.items()}},
+                              "ms_per_frame": round(ms_sd / K2, 4)},
+        "dense_dda_step": {"rays_per_s": round(n * K2 * world / (ms_dense / 1e3), 1),
+                           "ms_per_step": round(ms_dense / K2, 4)},
         "render_only_step": {
             "note": "vdb rebuild + hdda_render: the walk, then runs expanded from the lattice "
                     "table and composited in one kernel; no sample, scan or host read-back",
@@ -631,10 +661,10 @@ def run_ours(args):
             "vs_step": round(ms / ms_r, 3),
             "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}
                         for k, v in kern_r.items()},
-            "render_tinst_s": (round(render_evals * COMPOSITE_FP32_PER_BLOB
+            "render_fp32_tops": (round(render_evals * COMPOSITE_FP32_PER_BLOB
                                      / (kern_r["hdda_render"][1] / kern_r["hdda_render"][0] / 1e3)
                                      / 1e12, 2) if "hdda_render" in kern_r else None)},
-        "hdda_vs_dense_sampler_speedup": round(ms_sd / max(3, K // 2) / (ms_sh / K), 3),
+        "hdda_vs_dense_sampler_speedup": round(ms_sd / K2 / (ms_sh / K), 3),
         "grid": {"vdb_bytes": grid_bytes, "vdb_plain_bytes": plain_bytes,
                  "dense_bytes": int(vstats.dense_bytes),
                  "n_leaves": int(vstats.n_leaves), "n_tiles": int(vstats.n_tiles)},
@@ -648,10 +678,32 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    if full:
+        line.update({
+            "hdda_plain_vdb_sampler": {"rays_per_s": round(n * K2 * world / (ms_sp / 1e3), 1),
+                                       "ms_per_frame": round(ms_sp / K2, 4),
+                                       "note": "HDDA on the plain VDB tree (8^3 leaves, 16^3-block "
+                                               "nodes), refinement masks off"},
+            "skip_form_samplers": {
+                "note": "Algorithm 2 control flow (leading empty regions in an inner loop); "
+                        "same samples",
+                "hdda_ms_per_frame": round(ms_ss / K2, 4),
+                "dense_ms_per_frame": round(ms_ds / K2, 4)},
+            "synchronous_step": {"note": "the same step through hdda_traverse_hdda, which reads "
+                                         "the sample total back to the host before compositing",
+                                 "ms_per_step": round(ms_sync / K2, 4)},
+            "incremental_update": upd,
+            "fused_step": {
+                "note": "vdb rebuild + hdda_traverse_composite: the walk and the tile scan, then "
+                        "one kernel that writes every sample at its CSR position and composites "
+                        "it (the same samples as the step, the render-only path's frame)",
+                "rays_per_s": round(n * K * world / (ms_f / 1e3), 1),
+                "ms_per_step": round(ms_f / K, 4),
+                "vs_step": round(ms / ms_f, 3),
+                "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}
+                            for k, v in kern_f.items()}},
+        })
+    return line
 
 
 def cpu_baseline(sc, ray_pair, stride):
@@ -820,9 +872,11 @@ def profile_step(args):
     print(f"profile step done: {o.shape[0]} rays, {s.total} samples")
 
 
-def run_batch(args):
+def run_batch(args, quick: bool = False) -> dict:
     """64 (scene, camera) jobs, 64^2..800^2 rays each, 1-4 cascade levels: one autotuned,
-    graph-captured batch launch per step against 64 separate single-call launches."""
+    graph-captured batch launch per step against 64 separate single-call launches.  quick:
+    a reduced tuning space (walk block 256, 32 or 64 rays per fetch, 2 or 4 emit warps, then
+    the control flow) and fewer timed launches, for the summary in the headline line."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -845,12 +899,16 @@ def run_batch(args):
     def make(cfg):
         return hdda.Batch(jobs, config=cfg, use_graph=True)
 
+    space = autotune.SPACE
+    if quick:
+        space = [(256, rpf, ew, autotune.WALK_BRANCH) for rpf in (32, 64) for ew in (2, 4)]
     t_tune = time.perf_counter()
-    best, timings = autotune.tune(make, autotune.signature(jobs), reps=5, warmup=2,
-                                  use_cache=False)
+    best, timings = autotune.tune(make, autotune.signature(jobs), space=space,
+                                  reps=3 if quick else 5, warmup=2, use_cache=False)
     t_tune = time.perf_counter() - t_tune
     b = make(best)
-    K, W = args.steps, args.warmup
+    K = min(args.steps, 20) if quick else args.steps
+    W = args.warmup
     for _ in range(W):
         b.launch()
     torch.cuda.synchronize()
@@ -881,7 +939,8 @@ def run_batch(args):
     e1.record()
     e1.synchronize()
     ms_sep = e0.elapsed_time(e1) / reps
-    print(json.dumps({
+    b.free()
+    return {
         "metric": "batched sampling: total rays/s of 64 mixed jobs in one graph launch",
         "value": round(n_rays / (ms_batch / 1e3), 1), "unit": "rays/s", "n_gpus": 1, "steps": K,
         "warmup": W, "ms_per_step": round(ms_batch, 4), "higher_is_better": True,
@@ -902,13 +961,21 @@ def run_batch(args):
                                    for k, v in sorted(timings.items())},
                      "key": "walk_block/rays_per_fetch/emit_warps/walk_variant (1 = skip)"},
         "clocks": clk,
-    }), flush=True)
-    b.free()
+    }
 
 
-def run_serve(args):
+# Offered load of the serving measurement: a stated constant, below the capacity of both
+# executor modes, so that the tail reflects queueing at a known load rather than a noisy
+# capacity estimate.
+SERVE_LOAD = 400.0   # requests per second
+
+
+def run_serve(args, quick: bool = False) -> dict:
     """Continuous-batching server: 8 resident scenes, Poisson arrivals of 200x200..1920x1080
-    requests (log-uniform sides) at 70 % of the measured capacity; p50/p99 latency."""
+    requests (log-uniform sides) at SERVE_LOAD requests/s; p50/p99 latency over three repeats
+    of the same request sequence, for both executor modes, and each mode's closed-loop
+    capacity (a burst, context only).  An unmeasured repeat comes first.  quick: 3 s of
+    arrivals per repeat instead of 6 s."""
     import math
     import random
 
@@ -929,36 +996,34 @@ def run_serve(args):
         pool.append((torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory()))
     slots = 4
     budget = 8 << 30
+    seconds = 3.0 if quick else 6.0
     pick = random.Random(7)
 
     def make(rid):
         o, d = pool[pick.randrange(len(pool))]
         return serve.Request(rid=rid, scene=pick.randrange(len(scene_list)), rays_o=o, rays_d=d)
 
-    def one_mode(mode, lam=None):
-        """Closed-loop capacity, then Poisson arrivals at `lam` (default 70 % of it); the
-        same request sequence in every mode."""
-        pick.seed(7)
-        ex = serve.GpuExecutor(scene_list, slots=slots, mode=mode)
-        ex.warm()
+    def capacity(ex):
         srv = serve.RenderServer(ex, slots=slots, budget_bytes=budget)
         for i in range(16):
             srv.submit(make(i))
         srv.drain()
-        burst = [make(100 + i) for i in range(96)]
+        burst = [make(100 + i) for i in range(48 if quick else 96)]
         t0 = time.perf_counter()
         for r in burst:
             srv.submit(r)
         srv.drain()
-        capacity = len(burst) / (time.perf_counter() - t0)
+        cap = len(burst) / (time.perf_counter() - t0)
         srv.close()
-        lam = lam or 0.7 * capacity
-        n_req = max(60, int(lam * 6.0))
+        return cap
+
+    def at_load(ex, lam):
+        """One repeat: the same Poisson arrival sequence (seed 1006) and request mix (seed 7)."""
+        pick.seed(7)
+        n_req = max(60, int(lam * seconds))
         gaps = np.random.default_rng(1006).exponential(1.0 / lam, size=n_req)
         srv = serve.RenderServer(ex, slots=slots, budget_bytes=budget, samples_per_ray_hint=40)
         reqs = [make(1000 + i) for i in range(n_req)]
-        clocks = ClockSampler(0)
-        clocks.start()
         t_start = time.perf_counter()
         t_next = t_start
         for r, g in zip(reqs, gaps):
@@ -970,35 +1035,47 @@ def run_serve(args):
             srv.submit(r)
         srv.drain(timeout=300)
         wall = max(r.done for r in reqs) - t_start
-        clk = clocks.stop()
         srv.close()
         measured = reqs[len(reqs) // 10:]   # drop the first 10 % (warm-up of the queue)
         summ = serve.summary(measured, wall * len(measured) / len(reqs))
-        return {"capacity_frames_per_s": round(capacity, 2),
-                "offered_load_frames_per_s": round(lam, 2), "requests": n_req,
-                "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "mean_ms": summ["mean_ms"],
+        return {"p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "mean_ms": summ["mean_ms"],
                 "frames_per_s": summ["frames_per_s"], "rays_per_s": summ["rays_per_s"],
                 "re_runs": summ["retries"], "errors": summ["errors"],
-                "max_concurrent": srv.max_concurrent, "admission_ticks": srv.ticks,
-                "clocks": clk}
+                "max_concurrent": srv.max_concurrent, "admission_ticks": srv.ticks}
 
-    res = one_mode("samples")
-    ren = one_mode("render")
-    ren_same = one_mode("render", lam=res["offered_load_frames_per_s"])
-    print(json.dumps({
+    clocks = ClockSampler(0)
+    clocks.start()
+    modes = {}
+    for mode in ("samples", "render"):
+        pick.seed(7)
+        ex = serve.GpuExecutor(scene_list, slots=slots, mode=mode)
+        ex.warm()
+        cap = capacity(ex)
+        at_load(ex, SERVE_LOAD)   # warm-up repeat: the allocator's pools grow to the mix
+        reps = [at_load(ex, SERVE_LOAD) for _ in range(3)]
+        p99 = [r["p99_ms"] for r in reps]
+        p50 = [r["p50_ms"] for r in reps]
+        modes[mode] = {
+            "p50_ms": round(statistics.median(p50), 3), "p99_ms": round(statistics.median(p99), 3),
+            "p99_spread": round((max(p99) - min(p99)) / statistics.median(p99), 3),
+            "repeats": reps, "capacity_frames_per_s": round(cap, 1)}
+    clk = clocks.stop()
+    return {
         "metric": "serving: p50/p99 latency and frames/s at a fixed offered load",
-        "value": res["p99_ms"], "unit": "ms (p99 latency)", "n_gpus": 1,
+        "value": modes["samples"]["p99_ms"], "unit": "ms (p99 latency)", "n_gpus": 1,
         "higher_is_better": False, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "8 resident scenes (4 tiny-type 64^3, 4 object-type 128^3), "
-                               "requests 200x200..1920x1080 log-uniform, traversal + composite",
+                               "requests 200x200..1920x1080 log-uniform",
                    "slots": slots, "memory_budget_bytes": budget,
-                   "offered_load_frames_per_s": res["offered_load_frames_per_s"],
-                   "requests": res["requests"], "arrivals": "Poisson (seed 1006)"},
-        **{k: v for k, v in res.items() if k not in ("offered_load_frames_per_s", "requests")},
-        "render_mode": {"note": "hdda_render: no sample buffers, no re-runs; at 70 % of its "
-                                "own capacity, and at the offered load above",
-                        "own_load": ren, "same_load": ren_same},
-    }), flush=True)
+                   "offered_load_frames_per_s": SERVE_LOAD,
+                   "seconds_per_repeat": seconds, "repeats": 3,
+                   "arrivals": "Poisson (seed 1006), the same sequence in every repeat, after "
+                               "one unmeasured repeat"},
+        "samples_mode": dict(modes["samples"], note="traversal + compositing through sample "
+                                                    "buffers"),
+        "render_mode": dict(modes["render"], note="hdda_render: no sample buffers, no re-runs"),
+        "clocks": clk,
+    }
 
 
 def main():
@@ -1007,10 +1084,10 @@ def main():
         profile_step(args)
         return
     if args.workload == "batch" and args.impl == "ours":
-        run_batch(args)
+        print(json.dumps(run_batch(args)), flush=True)
         return
     if args.workload == "serve" and args.impl == "ours":
-        run_serve(args)
+        print(json.dumps(run_serve(args)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
