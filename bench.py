@@ -61,7 +61,7 @@ PROFILED_COUNTERS = {
 # entry must be dropped whenever its kernel changes, and a workload without a capture
 # reports none.
 PROFILED_TRAFFIC = {
-    "object": {"hdda_emit": 269_582_080, "hdda_walk": 15_695_104},
+    "object": {"composite": 237_120_512, "hdda_emit": 269_582_080, "hdda_walk": 15_695_104},
     "unbounded": {"hdda_emit": 2_182_746_624, "hdda_walk": 26_170_880},
 }
 
@@ -87,6 +87,9 @@ def parse_args():
     ap.add_argument("--profile-step", choices=["hdda", "dense", "render"], default=None,
                     help="profiling aid: one count-only call, one warm-up step and one step of "
                          "the given path on camera 0, no timing, no JSON line")
+    ap.add_argument("--profile-rays", type=int, default=0,
+                    help="with --profile-step: only the first N rays of camera 0 (whole image "
+                         "rows from the top), a smaller case for multi-pass ncu captures")
     return ap.parse_args()
 
 
@@ -843,6 +846,8 @@ def profile_step(args):
 
     sc, cams, _, _ = frame_workload(args.workload)
     o, d = cams[0].rays()
+    if args.profile_rays > 0:
+        o, d = o[:args.profile_rays].copy(), d[:args.profile_rays].copy()
     O, D = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
     dense = torch.from_numpy(sc.occ).cuda()
     field = torch.from_numpy(sc.field).cuda()

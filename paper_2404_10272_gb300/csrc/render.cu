@@ -65,7 +65,7 @@ __device__ __forceinline__ int run_k(const uint2* sr, int own, int p, int& j) {
 }
 
 template <int kMode, bool kStore>
-__global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
+__global__ void __launch_bounds__(kRenderWarps * 32, 6) render_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, const uint8_t* __restrict__ nruns, const uint2* __restrict__ runs,
     const float* __restrict__ field, int G, float* __restrict__ rgba, bool count_evals,
@@ -91,14 +91,25 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
   const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
   const int64_t r = task * kRenderRays + lane;
   const bool has_ray = lane < kRenderRays && r < n;
-  Ray ray{};
-  const bool ok = has_ray && load_ray(ro, rd, r, ray);
+  bool ok = false;
   if (lane < kRenderRays) {
+    // the ray stays in shared memory only; a ray that needs another round of
+    // runs rebuilds its walk state from there
+    float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f};
+    if (has_ray) {
+      ok = true;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[c] = __ldg(ro + 3 * r + c);
+        d[c] = __ldg(rd + 3 * r + c);
+        ok &= isfinite(o[c]) && isfinite(d[c]);
+      }
+    }
     T_s[lane] = 1.f;
     C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float dd = fmaf(ray.d[0], ray.d[0], fmaf(ray.d[1], ray.d[1], ray.d[2] * ray.d[2]));
-    rs[lane][0] = make_float4(ray.o[0], ray.o[1], ray.o[2], ray.d[0]);
-    rs[lane][1] = make_float4(ray.d[1], ray.d[2], dd > 0.f ? 1.f / dd : 0.f, 0.f);
+    const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+    rs[lane][0] = make_float4(o[0], o[1], o[2], d[0]);
+    rs[lane][1] = make_float4(d[1], d[2], dd > 0.f ? 1.f / dd : 0.f, 0.f);
   }
   const int nr_all = ok ? (int)nruns[r] : 0;  // saturated at 255
   int nr = min(nr_all, kMaxRuns);
@@ -214,9 +225,20 @@ __global__ void __launch_bounds__(kRenderWarps * 32) render_kernel(
     const bool more = k_next < lat.K;
     if (!__any_sync(kFull, more)) break;
     nr = 0;
-    if (more)
+    if (more) {
+      Ray ray;
+      const float4 A = rs[lane][0], B = rs[lane][1];
+      const float o[3] = {A.x, A.y, A.z}, d[3] = {A.w, B.x, B.y};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {  // as load_ray (walk.cuh) sets them up
+        ray.o[c] = o[c];
+        ray.d[c] = d[c];
+        ray.neg[c] = d[c] < 0.f;
+        ray.inv[c] = 1.0f / d[c];
+      }
       k_next = walk_from<kMode, false>(g, global_tabs(g), lat, h, ray, k_next, sr + lane,
                                        kRenderRays, nr);
+    }
     __syncwarp();
   }
   if (has_ray) {
