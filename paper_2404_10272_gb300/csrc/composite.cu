@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kWarpsPerCta)
   __shared__ float s_T[kWarpsPerCta][kRaysPerWarp];
   __shared__ float4 s_C[kWarpsPerCta][kRaysPerWarp];
+  __shared__ uint16_t s_cand[kWarpsPerCta][kMaxGauss];  // the task's candidate blobs
   __shared__ float4 s_ray[kWarpsPerCta][kRaysPerWarp][2];  // {o, d.x}, {d.y, d.z, 1/|d|^2, -}
   const FieldSmem fs = stage_blobs(smem, field, G);
   __syncthreads();
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
     }
     const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
     rs[lane][0] = make_float4(o[0], o[1], o[2], d[0]);
-    rs[lane][1] = make_float4(d[1], d[2], dd > 0.f ? 1.f / dd : 0.f, 0.f);
+    rs[lane][1] = make_float4(d[1], d[2], dd > 1e-30f ? 1.f / dd : 0.f, 0.f);
     T_s[lane] = 1.f;
     C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -71,6 +72,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
   const int s1 = (int)(__shfl_sync(kFull, sb, 1) - wbeg), s2 = (int)(__shfl_sync(kFull, sb, 2) - wbeg),
             s3 = (int)(__shfl_sync(kFull, sb, 3) - wbeg);
   const int total = (int)(wend - wbeg);
+  // a task of more than two chunks first narrows the field to the blobs near its rays'
+  // lines; a shorter one tests every blob in its chunks (the narrowing would cost more
+  // than it saves)
+  uint16_t* cand = s_cand[wib];
+  int ncand = G;
+  if (total > 2 * kChunk) {
+    ncand = task_candidates(fs, G, rs, (int)min((int64_t)kRaysPerWarp, n - wg * kRaysPerWarp),
+                            cand);
+  } else {
+    for (int q = lane; q < G; q += 32) cand[q] = (uint16_t)q;
+    __syncwarp();
+  }
   // the next chunk's interval ends are loaded one chunk ahead, so their
   // DRAM latency overlaps the current chunk's field evaluation
   float n0a = 0.f, n1a = 0.f, n0b = 0.f, n1b = 0.f;
@@ -109,7 +122,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
         e[h].pz = fmaf(tm, B.y, A.z);
       }
     }
-    evals += composite_chunk2(fs, G, nlive, e[0], e[1], rs, T_s, C_s);
+    evals += composite_chunk2(fs, cand, ncand, nlive, e[0], e[1], rs, T_s, C_s);
   }
   if (has_ray) {
     const float4 acc = C_s[lane];

@@ -19,9 +19,11 @@
 // ray's transmittance so far and its colour sum are carried in shared memory
 // (T_s, C_s, indexed by the ray's slot in the warp) from chunk to chunk.
 //
-// Blob culling: before evaluating a chunk, the warp keeps, in a shared-memory
-// list, only the blobs whose centre lies within kCullSigmas standard
-// deviations of the chunk's points: of the segments of the (one or two)
+// Blob culling, in two stages.  Per warp task, the blobs within reach of the
+// lines of the task's rays become its candidates (a list of indices).  Before
+// evaluating a chunk, the warp keeps, in a shared-memory list, only the
+// candidates whose centre lies within kCullSigmas standard deviations of the
+// chunk's points: of the segments of the (one or two)
 // rays the points lie on, between the smallest and largest midpoint
 // parameter of each ray's samples in the chunk (single-instruction warp
 // reductions over binary32, redux.sync.{min,max}.f32), or of the points'
@@ -113,6 +115,29 @@ __device__ __forceinline__ float warp_max(float v) {
 
 __device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
 
+// Opacity 1 - exp(-tau) of two intervals at once.  For |tau| < 1/2 it is the
+// Taylor series of -expm1(-tau) = tau * sum_k (-tau)^k / (k+1)!, k = 0..7,
+// in Horner form (the first term left out, (tau/2)^8 / 9! < 1.1e-8, is far
+// below binary32 rounding), which keeps small opacities accurate to a few
+// ulp; beyond, 1 - exp2(-tau log2 e), whose absolute error of a few 1e-8 is
+// small against an opacity of at least 0.39.
+__device__ __forceinline__ float2 opacity2(float2 tau) {
+  const float2 x = make_float2(-tau.x, -tau.y);
+  float2 p = splat(1.f / 40320.f);  // 1/8!
+  p = __ffma2_rn(p, x, splat(1.f / 5040.f));
+  p = __ffma2_rn(p, x, splat(1.f / 720.f));
+  p = __ffma2_rn(p, x, splat(1.f / 120.f));
+  p = __ffma2_rn(p, x, splat(1.f / 24.f));
+  p = __ffma2_rn(p, x, splat(1.f / 6.f));
+  p = __ffma2_rn(p, x, splat(0.5f));
+  p = __ffma2_rn(p, x, splat(1.f));
+  const float2 series = __fmul2_rn(tau, p);
+  const float2 big = make_float2(1.f - ex2_approx(-1.4426950408889634f * tau.x),
+                                 1.f - ex2_approx(-1.4426950408889634f * tau.y));
+  return make_float2(fabsf(tau.x) < 0.5f ? series.x : big.x,
+                     fabsf(tau.y) < 0.5f ? series.y : big.y);
+}
+
 // The part of one ray that a chunk's samples of it lie on: centre point c,
 // half-length hh in the ray's parameter, direction d and 1 / |d|^2.
 struct Segment {
@@ -157,16 +182,52 @@ struct Elem {
   int own;
 };
 
+// The blobs within reach of the lines of a warp task's rays, as a list of
+// blob indices in `cand` (in blob order); returns their number.  Every
+// sample of a ray lies on its line (up to binary32 rounding, which the
+// margin covers: a sample within reach of a blob is at most reach + |mu|
+// from the origin), so a chunk only has to test these candidates.  rs[slot]
+// holds {o, d.x}, {d.y, d.z, 1/|d|^2, -} of the task's `nrays` rays.
+__device__ __forceinline__ int task_candidates(const FieldSmem& fs, int G,
+                                               const float4 (*rs)[2], int nrays,
+                                               uint16_t* cand) {
+  const int lane = threadIdx.x & 31;
+  int n = 0;
+  for (int q0 = 0; q0 < G; q0 += 32) {
+    const int q = q0 + lane;
+    bool near = false;
+    if (q < G) {
+      const float4 c = fs.cull[q].v;  // -mu, reach
+      const float mu_max = fmaxf(fabsf(c.x), fmaxf(fabsf(c.y), fabsf(c.z)));
+      for (int r = 0; r < nrays; ++r) {
+        const float4 A = rs[r][0], B = rs[r][1];
+        const float wx = A.x + c.x, wy = A.y + c.y, wz = A.z + c.z;  // o - mu
+        const float u = -fmaf(wx, A.w, fmaf(wy, B.x, wz * B.y)) * B.z;
+        const float qx = fmaf(u, A.w, wx), qy = fmaf(u, B.x, wy), qz = fmaf(u, B.y, wz);
+        const float o_max = fmaxf(fabsf(A.x), fmaxf(fabsf(A.y), fabsf(A.z)));
+        const float reach = c.w + 2e-5f * (1.f + o_max + mu_max + c.w);
+        near |= fmaf(qx, qx, fmaf(qy, qy, qz * qz)) <= reach * reach;
+      }
+    }
+    const unsigned ball = __ballot_sync(kFieldFull, near);
+    if (near) cand[n + __popc(ball & ((1u << lane) - 1u))] = (uint16_t)q;
+    n += __popc(ball);
+  }
+  __syncwarp();
+  return n;
+}
+
 // One 64-sample chunk.  Lane l holds the chunk's samples 2l (e0) and
 // 2l + 1 (e1); samples below `nlive` are live, the rest padding (live
 // samples come first and are in ray order, so a ray's samples are
 // consecutive).  Updates T_s[own] and C_s[own] of every ray the chunk
-// touches.  Returns the chunk's blob evaluations (live samples x kept
-// blobs), the same on every lane.
-__device__ __forceinline__ int composite_chunk2(const FieldSmem& fs, int G, int nlive,
-                                                const Elem& e0, const Elem& e1,
-                                                const float4 (*rs)[2], float* T_s,
-                                                float4* C_s) {
+// touches.  `cand` lists the task's candidate blobs (task_candidates).
+// Returns the chunk's blob evaluations (live samples x kept blobs), the same
+// on every lane.
+__device__ __forceinline__ int composite_chunk2(const FieldSmem& fs, const uint16_t* cand,
+                                                int ncand, int nlive, const Elem& e0,
+                                                const Elem& e1, const float4 (*rs)[2],
+                                                float* T_s, float4* C_s) {
   const int lane = threadIdx.x & 31;
   const bool live0 = 2 * lane < nlive, live1 = 2 * lane + 1 < nlive;
   float2 sig = splat(0.f), cr = sig, cg = sig, cb = sig;
@@ -205,10 +266,12 @@ __device__ __forceinline__ int composite_chunk2(const FieldSmem& fs, int G, int 
       bz1 = warp_max(fmaxf(live0 ? e0.pz : -INFINITY, live1 ? e1.pz : -INFINITY));
     }
     BlobRec* kept = fs.kept;
-    for (int q0 = 0; q0 < G; q0 += 32) {
-      const int q = q0 + lane;
+    for (int i0 = 0; i0 < ncand; i0 += 32) {
+      const int i = i0 + lane;
       bool near = false;
-      if (q < G) {
+      int q = 0;
+      if (i < ncand) {
+        q = cand[i];
         const float4 c = fs.cull[q].v;  // -mu, reach
         if (segs) {
           const float ra = c.w + epsA;
@@ -251,17 +314,18 @@ __device__ __forceinline__ int composite_chunk2(const FieldSmem& fs, int G, int 
     __syncwarp();
   }
   // opacity and colour weight of each element
+  const float2 al = opacity2(make_float2(sig.x * (e0.a1 - e0.a0), sig.y * (e1.a1 - e1.a0)));
   float alpha0 = 0.f, alpha1 = 0.f;
   float3 w0 = make_float3(0.f, 0.f, 0.f), w1 = w0;
   if (live0) {
-    alpha0 = -expm1f(-sig.x * (e0.a1 - e0.a0));
+    alpha0 = al.x;
     if (sig.x > 0.f) {
       const float inv = __fdividef(alpha0, sig.x);
       w0 = make_float3(cr.x * inv, cg.x * inv, cb.x * inv);
     }
   }
   if (live1) {
-    alpha1 = -expm1f(-sig.y * (e1.a1 - e1.a0));
+    alpha1 = al.y;
     if (sig.y > 0.f) {
       const float inv = __fdividef(alpha1, sig.y);
       w1 = make_float3(cr.y * inv, cg.y * inv, cb.y * inv);

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32, 6) render_kernel(
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kRenderWarps)
   __shared__ float s_T[kRenderWarps][kRenderRays];
   __shared__ float4 s_C[kRenderWarps][kRenderRays];
+  __shared__ uint16_t s_cand[kRenderWarps][kMaxGauss];  // the task's candidate blobs
   __shared__ float4 s_ray[kRenderWarps][kRenderRays][2];  // {o, d.x}, {d.y, d.z, 1/|d|^2, -}
   __shared__ int64_t s_gbase[kRenderWarps][kRenderRays];  // storing form: output of position 0
   // run j of ray slot i at [j * kRenderRays + i]: {first k, first position}
@@ -109,8 +110,12 @@ __global__ void __launch_bounds__(kRenderWarps * 32, 6) render_kernel(
     C_s[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     const float dd = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
     rs[lane][0] = make_float4(o[0], o[1], o[2], d[0]);
-    rs[lane][1] = make_float4(d[1], d[2], dd > 0.f ? 1.f / dd : 0.f, 0.f);
+    rs[lane][1] = make_float4(d[1], d[2], dd > 1e-30f ? 1.f / dd : 0.f, 0.f);
   }
+  __syncwarp();
+  uint16_t* cand = s_cand[wib];
+  const int ncand =
+      task_candidates(fs, G, rs, (int)min((int64_t)kRenderRays, n - task * kRenderRays), cand);
   const int nr_all = ok ? (int)nruns[r] : 0;  // saturated at 255
   int nr = min(nr_all, kMaxRuns);
   for (int j = 0; j < nr; ++j) sr[j * kRenderRays + lane] = __ldg(runs + (int64_t)j * n + r);
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32, 6) render_kernel(
           }
         }
       }
-      evals += composite_chunk2(fs, G, min(kChunk, W - base), e[0], e[1], rs, T_s, C_s);
+      evals += composite_chunk2(fs, cand, ncand, min(kChunk, W - base), e[0], e[1], rs, T_s, C_s);
     }
     if constexpr (kStore) gofs += cnt;  // this round's samples of the lane's ray are written
     const bool more = k_next < lat.K;
