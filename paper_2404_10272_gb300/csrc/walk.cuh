@@ -769,9 +769,12 @@ int launch_walk(const WalkArgs& w, size_t smem, cudaStream_t s) {
   HDDA_CUDA_TRY(cudaGetDevice(&dev));
   HDDA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HDDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkBS, smem));
-  // one resident wave, but no more CTAs than 32-ray tiles: a small call is still
-  // spread over many SMs (its warps take tiles from the shared counter)
-  const int64_t want = (w.n + 31) / 32;
+  // one resident wave, but no more CTAs than one per eight 32-ray tiles: a small call
+  // is still spread over several SMs (its warps take tiles from the shared counter)
+  // without every SM staging the tables for warps that find no tile.  On the 96x96
+  // frame (288 tiles) the walk takes 0.0745 ms this way, 0.0792 ms with a CTA per
+  // tile and 0.0851 ms with a CTA per 32 tiles.
+  const int64_t want = ((w.n + 31) / 32 + 7) / 8;
   const int64_t full = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   const unsigned grid = (unsigned)(want < full ? want : full);
   kern<<<grid, kWalkBS, smem, s>>>(w.ro, w.rd, w.n, w.g, w.lat, w.counts, w.nruns, w.runs,
