@@ -979,7 +979,7 @@ def run_serve(args, quick: bool = False) -> dict:
     """Continuous-batching server: 8 resident scenes, Poisson arrivals of 200x200..1920x1080
     requests (log-uniform sides) at SERVE_LOAD requests/s; p50/p99 latency over three repeats
     of the same request sequence, for both executor modes, and each mode's closed-loop
-    capacity (a burst, context only).  An unmeasured repeat comes first.  quick: 3 s of
+    capacity (a burst, context only).  An unmeasured repeat comes first.  quick: 2.5 s of
     arrivals per repeat instead of 6 s."""
     import math
     import random
@@ -1001,7 +1001,7 @@ def run_serve(args, quick: bool = False) -> dict:
         pool.append((torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory()))
     slots = 4
     budget = 8 << 30
-    seconds = 3.0 if quick else 6.0
+    seconds = 2.5 if quick else 6.0
     pick = random.Random(7)
 
     def make(rid):
@@ -1051,7 +1051,7 @@ def run_serve(args, quick: bool = False) -> dict:
     clocks = ClockSampler(0)
     clocks.start()
     modes = {}
-    for mode in ("samples", "render"):
+    for mode in ("samples", "batched", "render"):
         pick.seed(7)
         ex = serve.GpuExecutor(scene_list, slots=slots, mode=mode)
         ex.warm()
@@ -1077,7 +1077,10 @@ def run_serve(args, quick: bool = False) -> dict:
                    "arrivals": "Poisson (seed 1006), the same sequence in every repeat, after "
                                "one unmeasured repeat"},
         "samples_mode": dict(modes["samples"], note="traversal + compositing through sample "
-                                                    "buffers"),
+                                                    "buffers, one request per slot"),
+        "batched_mode": dict(modes["batched"], note="a slot samples every ready request (up to "
+                                                    "8) in one hdda_batch launch, then "
+                                                    "composites each frame"),
         "render_mode": dict(modes["render"], note="hdda_render: no sample buffers, no re-runs"),
         "clocks": clk,
     }

@@ -387,7 +387,8 @@ typedef struct hdda_batch hdda_batch;  /* opaque, library-owned */
 
 /* Builds a batch plan for `n_jobs` jobs (HOST array, 1..4096); cfg (HOST) may
  * be NULL for {256, 64, 4, 1, HDDA_WALK_BRANCH}.  Looks up each job's lattice (synchronising
- * once per new parameter set) and synchronises the stream once. */
+ * once per new parameter set) and synchronises the stream once.  Scratch: plain device
+ * memory for a graph batch, the stream-ordered allocator of `stream` otherwise. */
 int hdda_batch_create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg,
                       hdda_batch** out, hdda_stream_t stream);
 
@@ -401,7 +402,11 @@ int hdda_batch_launch(hdda_batch* batch, hdda_stream_t stream);
 int hdda_batch_results(hdda_batch* batch, int64_t* totals, uint32_t* status,
                        hdda_stream_t stream);
 
-/* Frees a batch (waits for the device).  NULL is a no-op. */
+/* Frees a batch.  A batch made with use_graph = 0 returns its scratch to the
+ * stream-ordered allocator on the stream it was created on, after the work
+ * queued there (no synchronisation; launch such a batch only on that stream
+ * or order other streams after it); a graph batch waits for the device and
+ * frees plain device memory.  NULL is a no-op. */
 void hdda_batch_free(hdda_batch* batch);
 
 /*
@@ -417,9 +422,11 @@ void hdda_batch_free(hdda_batch* batch);
  *   offsets         device int64 [n_rays + 1] (as written by a traversal)
  *   t0, t1          device float samples
  *   field           device float [n_gauss][8] = mu_x, mu_y, mu_z, s, a, r, g, b,
- *                   with s > 0 and a >= 0.  Blobs farther than 7 s from every
- *                   sample of a 32-sample chunk are skipped for that chunk
- *                   (weight below a * e^-24.5)
+ *                   with s > 0 and a >= 0.  A blob is skipped for a group of
+ *                   64 consecutive samples when it lies farther than 7 s from
+ *                   every one of them (its weight there is below a * e^-24.5);
+ *                   the distance tests keep a small margin for rounding, so
+ *                   no blob within 7 s of a sample is skipped
  *   n_gauss         0..256
  *   rgba_out        device float [n_rays][4]
  * Stream-ordered, no synchronisation.

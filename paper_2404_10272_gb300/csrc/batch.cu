@@ -194,6 +194,10 @@ struct hdda_batch {
   int64_t* tile0 = nullptr;      // device [J + 1]
   char* scratch = nullptr;
   size_t scratch_bytes = 0;
+  // a batch without a graph takes its scratch from the stream-ordered allocator of
+  // the stream it was created on and returns it there
+  cudaStream_t alloc_stream = nullptr;
+  bool async_scratch = false;
   // carved from scratch
   unsigned* counter = nullptr;
   unsigned* status = nullptr;
@@ -392,10 +396,17 @@ int create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg, hdda_
                      a256((size_t)slots) + a256(sizeof(uint2) * kMaxRuns * (size_t)slots) +
                      a256(8 * (size_t)n_jobs) + a256(4 * (size_t)n_jobs) +
                      a256(sizeof(JobDev) * n_jobs) + a256(8 * (size_t)(n_jobs + 1));
-  cudaError_t e = cudaMalloc(&b->scratch, b->scratch_bytes);
+  // A graph keeps the addresses it was captured with, so a graph batch owns plain device
+  // memory; any other batch draws from the stream-ordered pool, so that creating and freeing
+  // one per request group (a server's admission tick) never synchronises the device.
+  b->async_scratch = !c.use_graph;
+  b->alloc_stream = s;
+  cudaError_t e = b->async_scratch ? cudaMallocAsync(&b->scratch, b->scratch_bytes, s)
+                                   : cudaMalloc(&b->scratch, b->scratch_bytes);
   if (e != cudaSuccess) {
+    b->scratch = nullptr;
     delete b;
-    return cuda_error(e, "cudaMalloc(batch)");
+    return cuda_error(e, "batch scratch allocation");
   }
   char* p = b->scratch;
   b->counter = reinterpret_cast<unsigned*>(p);
@@ -519,8 +530,12 @@ extern "C" void hdda_batch_free(hdda_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->scratch) {
-    cudaDeviceSynchronize();
-    cudaFree(b->scratch);
+    if (b->async_scratch) {
+      cudaFreeAsync(b->scratch, b->alloc_stream);  // after the batch's work on that stream
+    } else {
+      cudaDeviceSynchronize();
+      cudaFree(b->scratch);
+    }
   }
   delete b;
 }

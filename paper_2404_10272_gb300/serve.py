@@ -9,7 +9,7 @@ while others are running join them on the GPU instead of waiting for a batch
 boundary.  Each admission point takes every queued request that fits, in
 order (one "tick").
 
-Two executor modes:
+Three executor modes:
   "samples"  the frame goes through the sample buffers (traversal, then
              compositing), as the paper's renderer does.  The estimate is rays
              x (rays, offsets, colours, traversal scratch) plus samples x 12
@@ -17,6 +17,13 @@ Two executor modes:
              maximum over completed requests, plus headroom.  If a frame needs
              more samples than reserved, the sampler reports the exact total
              and the slot re-runs at that size.
+  "batched"  as "samples", but a slot takes every request that is ready when
+             it frees up (up to `max_batch`, one admission tick's worth) and
+             samples all of them in ONE batched launch (hdda_batch: the
+             requests' rays are cut into 32-ray tiles that persistent warps
+             take from one counter, across requests and scenes), then
+             composites each frame; a frame that outgrew its reservation is
+             re-run alone at the exact size.
   "render"   the render-only path (hdda_render): no sample buffers, so a
              request costs a fixed number of bytes per ray, never re-runs, and
              the library does not wait for the device before the frame's copy.
@@ -138,8 +145,10 @@ class RenderServer:
     slot's stream and fills req.rgba / req.samples (GpuExecutor below); it may raise
     NeedMore(samples) to ask for an exact re-run."""
 
-    def __init__(self, executor, slots: int, budget_bytes: int, samples_per_ray_hint: float = 64.0):
+    def __init__(self, executor, slots: int, budget_bytes: int, samples_per_ray_hint: float = 64.0,
+                 max_batch: int = 8):
         self.exec = executor
+        self.max_batch = max_batch if getattr(executor, "batched", False) else 1
         self.adm = Admission(budget_bytes, slots, samples_per_ray_hint,
                              bytes_per_ray=getattr(executor, "bytes_per_ray", BYTES_PER_RAY),
                              bytes_per_sample=getattr(executor, "bytes_per_sample",
@@ -180,24 +189,44 @@ class RenderServer:
                     self.cv.wait()
                 if self.stopping and not self.ready:
                     return
-                req = self.ready.popleft()
-            while True:
+                group = [self.ready.popleft() for _ in range(min(len(self.ready), self.max_batch))]
+            rerun = group
+            if self.max_batch > 1:
                 try:
-                    self.exec(slot, req, req.reserved)
-                    break
-                except NeedMore as more:
-                    req.retries += 1
-                    with self.cv:
-                        self.adm.resize(req, more.samples)
-                except Exception as e:  # the request fails, the server goes on
-                    req.error = repr(e)
-                    break
-            req.done = time.perf_counter()
+                    rerun = [r for r, samples in self.exec.batch_call(slot, group)]
+                except Exception as e:  # the group fails, the server goes on
+                    for r in group:
+                        r.error = repr(e)
+                    rerun = []
+                for r in rerun:  # frames that outgrew their reservation, alone at the exact size
+                    r.retries += 1
+                with self.cv:
+                    for r in rerun:
+                        self.adm.resize(r, r.samples)
+            for req in rerun:
+                self._run_one(slot, req)
+            now = time.perf_counter()
             with self.cv:
-                self.adm.release(req)
-                self.completed.append(req)
+                for req in group:
+                    req.done = now if req.done == 0.0 else req.done
+                    self.adm.release(req)
+                    self.completed.append(req)
                 self._tick()
                 self.cv.notify_all()
+
+    def _run_one(self, slot: int, req: Request) -> None:
+        while True:
+            try:
+                self.exec(slot, req, req.reserved)
+                break
+            except NeedMore as more:
+                req.retries += 1
+                with self.cv:
+                    self.adm.resize(req, more.samples)
+            except Exception as e:  # the request fails, the server goes on
+                req.error = repr(e)
+                break
+        req.done = time.perf_counter()
 
     def drain(self, timeout: float = 120.0) -> None:
         t_end = time.perf_counter() + timeout
@@ -227,11 +256,12 @@ class GpuExecutor:
     def __init__(self, scene_list, slots: int, mode: str = "samples"):
         import torch
         from . import hdda
-        if mode not in ("samples", "render"):
+        if mode not in ("samples", "batched", "render"):
             raise ValueError(f"unknown mode {mode!r}")
         self.mode = mode
-        self.bytes_per_ray = BYTES_PER_RAY if mode == "samples" else BYTES_PER_RAY_RENDER
-        self.bytes_per_sample = BYTES_PER_SAMPLE if mode == "samples" else 0
+        self.batched = mode == "batched"
+        self.bytes_per_ray = BYTES_PER_RAY if mode != "render" else BYTES_PER_RAY_RENDER
+        self.bytes_per_sample = BYTES_PER_SAMPLE if mode != "render" else 0
         self.torch = torch
         self.hdda = hdda
         self.grids, self.fields, self.params = [], [], []
@@ -278,6 +308,45 @@ class GpuExecutor:
             s.synchronize()
         req.samples = smp.total
         req.rgba = host
+
+    def batch_call(self, slot: int, reqs: list) -> list:
+        """Samples every request of the group in one batched launch on the slot's stream,
+        then composites each frame.  Returns [(request, samples)] for the frames whose
+        samples did not fit their reservation (req.samples holds the exact count)."""
+        torch, hdda = self.torch, self.hdda
+        s = self.streams[slot]
+        with torch.cuda.stream(s):
+            jobs = []
+            for req in reqs:
+                n = req.n_rays
+                cap = max(1, (req.reserved - n * BYTES_PER_RAY) // BYTES_PER_SAMPLE)
+                jobs.append(dict(rays_o=req.rays_o.to("cuda", non_blocking=True),
+                                 rays_d=req.rays_d.to("cuda", non_blocking=True),
+                                 grid=self.grids[req.scene], params=self.params[req.scene],
+                                 out=hdda.alloc_samples(n, cap)))
+            b = hdda.Batch(jobs, use_graph=False, stream=s)
+            try:
+                b.launch(stream=s)
+                totals, status = b.results(stream=s, check=False)
+            finally:
+                b.free()
+            over, hosts = [], []
+            for req, jb, tot, st in zip(reqs, jobs, totals, status):
+                req.samples = tot
+                if st != hdda.OK:
+                    over.append((req, tot))
+                    hosts.append(None)
+                    continue
+                rgba = hdda.composite(jb["rays_o"], jb["rays_d"], jb["out"],
+                                      self.fields[req.scene], stream=s)
+                host = torch.empty((req.n_rays, 4), dtype=torch.float32, pin_memory=True)
+                host.copy_(rgba, non_blocking=True)
+                hosts.append(host)
+            s.synchronize()
+        for req, host in zip(reqs, hosts):
+            if host is not None:
+                req.rgba = host
+        return over
 
     def _render(self, slot: int, req: Request) -> None:
         torch, hdda = self.torch, self.hdda

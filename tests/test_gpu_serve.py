@@ -91,3 +91,40 @@ def test_render_mode_alone_equals_mixed_and_direct(setup):
     s = hdda.traverse_hdda(o.cuda(), d.cuda(), ex.grids[1], prm)
     two = hdda.composite(o.cuda(), d.cuda(), s, ex.fields[1]).cpu()
     assert (two - alone.rgba).abs().max().item() <= 2 * TOL
+
+
+def test_batched_mode_alone_equals_mixed_and_direct(setup):
+    # "batched": a slot samples every ready request of a tick in one hdda_batch launch
+    # (work stealing across requests and scenes), then composites each frame.  A frame
+    # is the same alone, batched with others, and through the direct API; frames that
+    # outgrow their reservation re-run alone at the exact size.
+    hdda, sc, _ = setup
+    ex = serve.GpuExecutor(sc, slots=2, mode="batched")
+    ex.warm()
+    o, d = _rays(3, 320, 240)
+    alone = serve.Request(rid=0, scene=1, rays_o=o, rays_d=d)
+    srv = serve.RenderServer(ex, slots=2, budget_bytes=4 << 30)
+    srv.submit(alone)
+    srv.close()
+    assert alone.error is None
+    srv = serve.RenderServer(ex, slots=2, budget_bytes=4 << 30, samples_per_ray_hint=2,
+                             max_batch=8)
+    mix = []
+    for i in range(14):
+        oo, dd = _rays(300 + i, 64 + 40 * i, 48 + 30 * i)
+        mix.append(serve.Request(rid=i + 1, scene=i % 2, rays_o=oo, rays_d=dd))
+    target = serve.Request(rid=99, scene=1, rays_o=o, rays_d=d)
+    for r in mix[:7] + [target] + mix[7:]:
+        srv.submit(r)
+    srv.close()
+    assert all(r.error is None for r in mix + [target])
+    assert target.samples == alone.samples
+    assert torch.equal(target.rgba, alone.rgba)
+    # the low hint makes some frames outgrow their reservation: they re-ran alone
+    assert sum(r.retries for r in mix + [target]) > 0
+    p = sc[1].params
+    prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    s = hdda.traverse_hdda(o.cuda(), d.cuda(), ex.grids[1], prm)
+    direct = hdda.composite(o.cuda(), d.cuda(), s, ex.fields[1]).cpu()
+    assert s.total == alone.samples
+    assert torch.equal(direct, alone.rgba)
