@@ -11,7 +11,7 @@
 // object-centric frame, 750 in the unbounded one) keep the last tasks short.
 // The task's rays (origin, direction) are staged in shared memory, and
 // every lane keeps the rays' first sample positions in registers, so a
-// sample finds its ray by three compares.
+// sample finds its ray by compares.
 #include "field.cuh"
 
 namespace hdda {
@@ -29,7 +29,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
     const int64_t* __restrict__ offsets, const float* __restrict__ t0,
     const float* __restrict__ t1, const float* __restrict__ field, int G,
     float* __restrict__ rgba, bool count_evals) {
-  static_assert(kRaysPerWarp == 4, "the owner lookup below compares against three ray starts");
   extern __shared__ __align__(16) unsigned char smem[];  // field_smem_bytes(G, kWarpsPerCta)
   __shared__ float s_T[kWarpsPerCta][kRaysPerWarp];
   __shared__ float4 s_C[kWarpsPerCta][kRaysPerWarp];
@@ -67,10 +66,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
   __syncwarp();
   const int64_t wbeg = __shfl_sync(kFull, sb, 0);
   const int64_t wend = __shfl_sync(kFull, se, kRaysPerWarp - 1);
-  // first sample of rays 1..3 relative to the warp's first sample (a task's
-  // samples fit in 32 bits)
-  const int s1 = (int)(__shfl_sync(kFull, sb, 1) - wbeg), s2 = (int)(__shfl_sync(kFull, sb, 2) - wbeg),
-            s3 = (int)(__shfl_sync(kFull, sb, 3) - wbeg);
+  // first sample of rays 1 .. kRaysPerWarp - 1 relative to the warp's first sample (a
+  // task's samples fit in 32 bits)
+  int sfirst[kRaysPerWarp];
+#pragma unroll
+  for (int i = 1; i < kRaysPerWarp; ++i) sfirst[i] = (int)(__shfl_sync(kFull, sb, i) - wbeg);
   const int total = (int)(wend - wbeg);
   // a task of more than two chunks first narrows the field to the blobs near its rays'
   // lines; a shorter one tests every blob in its chunks (the narrowing would cost more
@@ -111,7 +111,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, 8) composite_kernel(
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int p = base + 2 * lane + h;
-      const int own = (p >= s1) + (p >= s2) + (p >= s3);  // the last ray starting at or before p
+      int own = 0;  // the last ray starting at or before p
+#pragma unroll
+      for (int i = 1; i < kRaysPerWarp; ++i) own += p >= sfirst[i];
       e[h].own = own;
       e[h].px = e[h].py = e[h].pz = 0.f;
       if (p < total) {

@@ -200,10 +200,10 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
       occ = (w >> (lin & 31)) & 1u;
       break;
     }
-    // node level
+    // node level: L * N^3 <= 8 * 8^3 nodes and L * B^3 * 16 <= 2^28 leaf words, so
+    // every offset below fits 32 bits (cheaper address arithmetic than 64-bit)
     const int N = g.N;
-    const int64_t ng = (int64_t)l * N * N * N +
-                       ((i[0] >> 7) * N + (i[1] >> 7)) * N + (i[2] >> 7);
+    const int ng = l * N * N * N + ((i[0] >> 7) * N + (i[1] >> 7)) * N + (i[2] >> 7);
     const uint32_t st = ld<kSm>(tb.nstate + ng);
     if (st != kNodeMixed) {
       sz = kNodeVox;
@@ -240,7 +240,7 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
     const uint32_t leaf = ld<kSm>(tb.prefix + ng * kNodeWords + w) + __popc(cw & (bit - 1u));
     if constexpr (kMode == kModeVdbRefined) {
       // empty 4^3 cell, then an empty or fully occupied 2^3 cell of the leaf
-      const uint32_t* ls = g.lsub + (int64_t)leaf * kLeafSubWords;
+      const uint32_t* ls = g.lsub + leaf * (uint32_t)kLeafSubWords;
       const int c4 = (((i[0] >> 2) & 1) * 2 + ((i[1] >> 2) & 1)) * 2 + ((i[2] >> 2) & 1);
       if (!((__ldg(ls + 2) >> c4) & 1u)) {
         sz = 4;
@@ -257,11 +257,11 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
       }
     }
     const int v = ((i[0] & 7) * 8 + (i[1] & 7)) * 8 + (i[2] & 7);
-    const uint32_t lw = __ldg(g.leaves + (int64_t)leaf * kLeafWords + (v >> 5));
+    const uint32_t lw = __ldg(g.leaves + (leaf * (uint32_t)kLeafWords + (uint32_t)(v >> 5)));
     occ = (lw >> (v & 31)) & 1u;
   } while (false);
   const int R1 = g.R + 1;
-  const float* thr = tb.thr + (int64_t)l * 3 * R1;
+  const float* thr = tb.thr + l * 3 * R1;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int a0 = i[c] & -sz;
