@@ -130,3 +130,47 @@ def test_benchmark_step_full_size(H, which):
     err = np.abs(to_np(rgba)[sel].astype(np.float64) - want)
     assert err.max() <= TOL, err.max()
     assert want[:, 3].max() > 0.5
+
+
+def _random_samples(rng, n_rays, counts):
+    """Rays of random origin and (not unit) direction, one of them with a zero direction,
+    and per ray `counts[r]` intervals in random order: non-negative lengths, some of length
+    0, scattered over t in [0, 4)."""
+    o = rng.uniform(-1.5, 1.5, (n_rays, 3)).astype(np.float32)
+    d = rng.normal(size=(n_rays, 3)).astype(np.float32) * rng.uniform(0.5, 2.0, (n_rays, 1)).astype(np.float32)
+    d[n_rays // 2] = 0.0
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    S = int(off[-1])
+    t0 = rng.uniform(0.0, 4.0, S).astype(np.float32)
+    dt = rng.uniform(0.0, 0.02, S).astype(np.float32)
+    dt[rng.random(S) < 0.05] = 0.0
+    t1 = (t0 + dt).astype(np.float32)
+    return o, d, off, t0, t1
+
+
+@pytest.mark.parametrize("G", [1, 37, 64, 256])
+def test_culling_paths_on_unordered_samples(H, G):
+    # The compositor's culling takes different paths: chunks of one or two rays test blobs
+    # against the rays' segments, chunks of three rays or more against their bounding box;
+    # tasks longer than two chunks first narrow the field to the blobs near their rays'
+    # lines.  Rays here hold 0, 1, a few or hundreds of samples, in random order along the
+    # ray (the ABI does not ask for ascending t), so every path runs; pixels must stay within
+    # 1e-5 of the binary64 oracle, which sums every blob.
+    rng = np.random.default_rng(500 + G)
+    counts = rng.choice([0, 1, 3, 17, 70, 300], size=203, p=[0.15, 0.15, 0.2, 0.2, 0.2, 0.1])
+    o, d, off, t0, t1 = _random_samples(rng, counts.size, counts)
+    field = np.zeros((G, 8), np.float32)
+    field[:, :3] = rng.uniform(-2.0, 2.0, (G, 3))
+    field[:, 3] = rng.uniform(0.03, 0.4, G)
+    field[:, 4] = rng.uniform(0.5, 30.0, G)
+    field[:, 5:] = rng.uniform(0.0, 1.0, (G, 3))
+    s = H.alloc_samples(o.shape[0], max(1, int(off[-1])))
+    s.offsets.copy_(torch.from_numpy(off))
+    s.t0[:off[-1]].copy_(torch.from_numpy(t0))
+    s.t1[:off[-1]].copy_(torch.from_numpy(t1))
+    s.total = int(off[-1])
+    rgba = to_np(H.composite(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(), s,
+                             torch.from_numpy(field).cuda())).astype(np.float64)
+    ref = oracle.composite(o, d, off, t0, t1, field)
+    assert np.abs(rgba - ref).max() <= TOL, np.abs(rgba - ref).max()
+    assert ref[:, 3].max() > 0.05   # some pixels see the field
