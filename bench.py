@@ -53,16 +53,20 @@ KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # from the same ncu --set full captures (object frame, camera 0); dropped like the traffic
 # when a kernel changes.
 PROFILED_COUNTERS = {
-    "object": {"hdda_walk": {"l2_hit_pct": 37.6, "active_lanes_of_32": 24.59},
-               "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98}},
+    "object": {"hdda_walk": {"active_lanes_of_32": 24.60},
+               "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98},
+               "composite": {"active_lanes_of_32": 30.03}},
+    "unbounded": {"hdda_walk": {"active_lanes_of_32": 24.18},
+                  "hdda_emit": {"active_lanes_of_32": 29.74},
+                  "composite": {"active_lanes_of_32": 30.46}},
 }
 # DRAM bytes (read + write) per launch from ncu of a workload's step on camera 0 (the
 # capture commands are kept with the profile summaries), for the roofline's "traffic"; an
 # entry must be dropped whenever its kernel changes, and a workload without a capture
 # reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 237_120_512, "hdda_emit": 269_582_080, "hdda_walk": 15_695_104},
-    "unbounded": {"composite": 1_502_438_144, "hdda_emit": 2_185_679_616, "hdda_walk": 26_021_632},
+    "object": {"composite": 233_595_392, "hdda_emit": 269_224_960, "hdda_walk": 15_702_016},
+    "unbounded": {"composite": 1_502_086_656, "hdda_emit": 2_185_638_400, "hdda_walk": 26_044_672},
 }
 
 
