@@ -50,15 +50,15 @@ L2_FLUSH_BYTES = 256 << 20
 COMPOSITE_FP32_PER_BLOB = 11
 KERNELS_PER_TIMER = {"build_vdb": 4}   # the builder's timer spans four kernels
 # L2 hit rate and warp execution efficiency (active lanes per warp instruction) per kernel
-# from the same ncu --set full captures (object frame, camera 0); dropped like the traffic
-# when a kernel changes.
+# from the ncu --set full captures (object frame, camera 0; unbounded: its first 200 image
+# rows); dropped like the traffic when a kernel changes.
 PROFILED_COUNTERS = {
-    "object": {"hdda_walk": {"active_lanes_of_32": 24.60},
+    "object": {"hdda_walk": {"l2_hit_pct": 37.9, "active_lanes_of_32": 24.60},
                "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98},
-               "composite": {"active_lanes_of_32": 30.03}},
-    "unbounded": {"hdda_walk": {"active_lanes_of_32": 24.18},
-                  "hdda_emit": {"active_lanes_of_32": 29.74},
-                  "composite": {"active_lanes_of_32": 30.46}},
+               "composite": {"l2_hit_pct": 26.4, "active_lanes_of_32": 30.03}},
+    "unbounded": {"hdda_walk": {"l2_hit_pct": 44.5, "active_lanes_of_32": 24.18},
+                  "hdda_emit": {"l2_hit_pct": 10.3, "active_lanes_of_32": 29.74},
+                  "composite": {"l2_hit_pct": 16.6, "active_lanes_of_32": 30.46}},
 }
 # DRAM bytes (read + write) per launch from ncu of a workload's step on camera 0 (the
 # capture commands are kept with the profile summaries), for the roofline's "traffic"; an
