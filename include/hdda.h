@@ -106,6 +106,9 @@ typedef struct {
                             index thresholds, masks and leaves (Table 3)    */
     int64_t dense_bytes; /* levels * ceil(res^3 / 32) * 4: the dense bit
                             array the paper starts from (Table 3 caption)   */
+    int64_t map_bytes;   /* VDB: the region map HDDA reads with refinement
+                            on (HDDA_ARRAY_REGION_MAP), 2 bytes per 2^3
+                            cell per level; not part of `bytes`            */
 } hdda_grid_stats;
 
 /* Arrays of a grid that hdda_grid_copy_array can export. */
@@ -145,7 +148,16 @@ typedef enum {
        / 4 (a bit is set when the cell holds an occupied voxel); words 3-4 =
        64 bits over the 2^3-voxel cells again, set when all 8 voxels of the
        cell are occupied.                                                     */
-    HDDA_ARRAY_LEAF_SUB = 7
+    HDDA_ARRAY_LEAF_SUB = 7,
+    /* uint16 [levels][C][C][C], C = ceil(res / 2): the region map (VDB), one
+       entry per 2^3-voxel cell (voxel_c / 2 per axis).  Bits 8-15: log2 of
+       the edge of the coarsest uniform region of the refined tree holding
+       the cell: 7 = an empty or full 128^3 node, 5 / 4 = an empty 32^3 /
+       16^3 group, 3 = an empty or tiled 8^3 block, 2 = an empty 4^3 cell,
+       1 = an empty or full 2^3 cell, 0 = the cell is not uniform.  Bits 0-7:
+       voxel (x, y, z) of the cell is bit ((x%2)*2 + y%2)*2 + z%2; all eight
+       equal (0x00 or 0xff) when the region is uniform.                       */
+    HDDA_ARRAY_REGION_MAP = 8
 } hdda_array;
 
 /* Version string of the library. */
@@ -231,9 +243,11 @@ int hdda_grid_copy_array(const hdda_grid* grid, int which, void* dst, size_t byt
  * Chooses the hierarchy hdda_traverse_hdda walks on a VDB grid.  on = 1 (the
  * default): besides empty nodes, empty or tiled 8^3 blocks and single leaf
  * voxels, it also crosses empty 32^3 and 16^3 groups inside a node and
- * empty 4^3 and 2^3 cells inside a leaf in one step each, an octree-style
- * refinement of the VDB tree (Sec. 5 names finer subdivision as worth
- * studying).  on = 0: the plain tree of 8^3 leaves under 16^3-block nodes.
+ * empty 4^3 and empty or full 2^3 cells inside a leaf in one step each, an
+ * octree-style refinement of the VDB tree (Sec. 5 names finer subdivision
+ * as worth studying).  The walk finds each region in the region map
+ * (HDDA_ARRAY_REGION_MAP, built with the tree) by one lookup.  on = 0: the
+ * plain tree of 8^3 leaves under 16^3-block nodes, descended per region.
  * Results are identical either way.  Not for dense grids.
  */
 int hdda_grid_set_refine(hdda_grid* grid, int on);

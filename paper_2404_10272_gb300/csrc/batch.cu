@@ -295,7 +295,7 @@ int enqueue(const hdda_batch* b, cudaStream_t s) {
   switch (b->mode) {
     case kModeDense: launch_batch_walk<kModeDense>(b, s); break;
     case kModeVdb: launch_batch_walk<kModeVdb>(b, s); break;
-    default: launch_batch_walk<kModeVdbRefined>(b, s); break;
+    default: launch_batch_walk<kModeVdbMap>(b, s); break;
   }
   HDDA_CUDA_TRY(cudaGetLastError());
   tile_scan_kernel<<<1, kScanThreads, 0, s>>>(b->tile_sum, b->T, b->tile_prefix, b->total,
@@ -304,7 +304,7 @@ int enqueue(const hdda_batch* b, cudaStream_t s) {
   switch (b->mode) {
     case kModeDense: launch_batch_emit<kModeDense>(b, s); break;
     case kModeVdb: launch_batch_emit<kModeVdb>(b, s); break;
-    default: launch_batch_emit<kModeVdbRefined>(b, s); break;
+    default: launch_batch_emit<kModeVdbMap>(b, s); break;
   }
   HDDA_CUDA_TRY(cudaGetLastError());
   return HDDA_OK;
@@ -347,7 +347,7 @@ int create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg, hdda_
       return set_error(HDDA_ERR_INVALID_ARG, "job %d: grid lives on another device", j);
     const int m = jb.grid->kind == HDDA_GRID_DENSE
                       ? kModeDense
-                      : (jb.grid->refine ? kModeVdbRefined : kModeVdb);
+                      : (jb.grid->refine ? kModeVdbMap : kModeVdb);
     if (mode >= 0 && m != mode)
       return set_error(HDDA_ERR_INVALID_ARG, "job %d: all grids of a batch must be of one kind", j);
     mode = m;
@@ -447,7 +447,7 @@ int create(const hdda_job* jobs, int n_jobs, const hdda_batch_config* cfg, hdda_
         st = walk_grid_for_block<kModeVdb>(c.walk_block, skip, &b->walk_grid);
         break;
       default:
-        st = walk_grid_for_block<kModeVdbRefined>(c.walk_block, skip, &b->walk_grid);
+        st = walk_grid_for_block<kModeVdbMap>(c.walk_block, skip, &b->walk_grid);
         break;
     }
   }

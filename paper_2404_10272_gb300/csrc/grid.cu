@@ -15,11 +15,15 @@
 //                       leaf prefix per mask word, leaf and tile totals
 //   vdb_scatter_kernel  16 threads per partial block copy its mask into the
 //                       compact leaf pool
+//   region_map_kernel   one thread per 2^3-voxel cell: the refined tree's
+//                       region holding the cell, flattened into 16 bits
 // The node and scatter kernels also write the refinement masks (occupied
 // 32^3 and 16^3 groups per node, occupied 4^3 and 2^3 cells per leaf) that
 // let hierarchical DDA cross empty space in power-of-two steps below and
 // above the 8^3 leaf, in the manner of an octree (Sec. 5 suggests finer
-// subdivision).
+// subdivision).  The region map flattens the refined tree for the walk: a
+// ray point's region (its size and occupancy) is one 2-byte load there
+// instead of a descent through node, group, block, leaf and cell masks.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -417,6 +421,67 @@ __global__ void vdb_rewrite_leaves_kernel(int B, int N, const int64_t* __restric
 
 // ---------------------------------------------------------------------------
 // host side
+// The region map (layout in hdda_internal.cuh), written after the tree and
+// its refinement masks.  Each thread descends the refined tree from the
+// cell's first voxel, exactly as a walk over the tree would: node state,
+// empty 32^3 and 16^3 groups, empty or tiled 8^3 block, empty 4^3 cell,
+// empty or full 2^3 cell; a cell that is none of these keeps its 8 voxel
+// bits.  Voxels past the grid edge (odd R) are empty in the leaves.
+__global__ void region_map_kernel(GridDev g, uint16_t* __restrict__ rmap) {
+  const int C = (g.R + 1) >> 1;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)g.L * C * C * C) return;
+  int64_t q = idx;
+  const int a2 = (int)(q % C);
+  q /= C;
+  const int a1 = (int)(q % C);
+  q /= C;
+  const int a0 = (int)(q % C);
+  const int l = (int)(q / C);
+  const int i[3] = {2 * a0, 2 * a1, 2 * a2};
+  const int N = g.N;
+  const int ng = l * N * N * N + ((i[0] >> 7) * N + (i[1] >> 7)) * N + (i[2] >> 7);
+  uint32_t lg = 0, mask = 0;
+  do {
+    const uint32_t st = g.nstate[ng];
+    if (st != kNodeMixed) {
+      lg = kMapNodeLog2;
+      mask = st == kNodeFull ? 0xffu : 0u;
+      break;
+    }
+    const uint32_t* ns = g.nsuper + ng * kSuperWords;
+    const int g4 = (((i[0] >> 5) & 3) * 4 + ((i[1] >> 5) & 3)) * 4 + ((i[2] >> 5) & 3);
+    if (!((ns[g4 >> 5] >> (g4 & 31)) & 1u)) { lg = 5; break; }
+    const int g2 = (((i[0] >> 4) & 7) * 8 + ((i[1] >> 4) & 7)) * 8 + ((i[2] >> 4) & 7);
+    if (!((ns[2 + (g2 >> 5)] >> (g2 & 31)) & 1u)) { lg = 4; break; }
+    const int cell = (((i[0] >> 3) & 15) * 16 + ((i[1] >> 3) & 15)) * 16 + ((i[2] >> 3) & 15);
+    const int w = cell >> 5;
+    const uint32_t bit = 1u << (cell & 31);
+    const uint32_t cw = g.child[ng * kNodeWords + w];
+    if (!(cw & bit)) {
+      lg = 3;
+      mask = (g.tile[ng * kNodeWords + w] & bit) ? 0xffu : 0u;
+      break;
+    }
+    const uint32_t leaf = g.prefix[ng * kNodeWords + w] + __popc(cw & (bit - 1u));
+    const uint32_t* ls = g.lsub + leaf * (uint32_t)kLeafSubWords;
+    const int c4 = (((i[0] >> 2) & 1) * 2 + ((i[1] >> 2) & 1)) * 2 + ((i[2] >> 2) & 1);
+    if (!((ls[2] >> c4) & 1u)) { lg = 2; break; }
+    const int c2 = (((i[0] >> 1) & 3) * 4 + ((i[1] >> 1) & 3)) * 4 + ((i[2] >> 1) & 3);
+    lg = 1;
+    if (!((ls[c2 >> 5] >> (c2 & 31)) & 1u)) break;          // empty 2^3 cell
+    if ((ls[3 + (c2 >> 5)] >> (c2 & 31)) & 1u) { mask = 0xffu; break; }  // full 2^3 cell
+    lg = 0;
+    const uint32_t* lw = g.leaves + leaf * (uint32_t)kLeafWords;
+    for (int u = 0; u < 8; ++u) {
+      const int x = (i[0] & 7) + (u >> 2), y = (i[1] & 7) + ((u >> 1) & 1), z = (i[2] & 7) + (u & 1);
+      const int v = (x * 8 + y) * 8 + z;
+      mask |= ((lw[v >> 5] >> (v & 31)) & 1u) << u;
+    }
+  } while (false);
+  rmap[idx] = (uint16_t)((lg << 8) | mask);
+}
+
 // ---------------------------------------------------------------------------
 
 int validate(const uint8_t* dense, int levels, int res, const hdda_aabb* aabbs) {
@@ -465,6 +530,7 @@ size_t layout(hdda_grid* g, char* base) {
   carve(base, off, g->leaves, g->blocks_total() * kLeafWords, vdb);
   carve(base, off, g->nsuper, g->nodes_total() * kSuperWords, vdb);
   carve(base, off, g->lsub, g->blocks_total() * kLeafSubWords, vdb);
+  carve(base, off, g->rmap, g->map_cells(), vdb);
   carve(base, off, g->blk_masks, g->blocks_total() * kLeafWords, vdb);
   carve(base, off, g->blk_state, g->blocks_total(), vdb);
   carve(base, off, g->local_prefix, nw, vdb);
@@ -485,7 +551,7 @@ int launch_build(hdda_grid* g, const uint8_t* dense, cudaStream_t s) {
     HDDA_CUDA_TRY(cudaGetLastError());
   } else {
     const int64_t nblk = g->blocks_total();
-    KernelTimer kt("build_vdb", s);  // the four build kernels together
+    KernelTimer kt("build_vdb", s);  // the five build kernels together
     vdb_blocks_kernel<<<blocks_for(nblk * 32, 256), 256, 0, s>>>(dense, g->L, g->R, g->B,
                                                                  g->blk_masks, g->blk_state);
     HDDA_CUDA_TRY(cudaGetLastError());
@@ -499,6 +565,8 @@ int launch_build(hdda_grid* g, const uint8_t* dense, cudaStream_t s) {
     vdb_scatter_kernel<<<blocks_for(nblk * 16, 256), 256, 0, s>>>(
         g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves, g->lsub,
         nullptr);
+    HDDA_CUDA_TRY(cudaGetLastError());
+    region_map_kernel<<<blocks_for(g->map_cells(), 256), 256, 0, s>>>(g->view(), g->rmap);
     kt.stop();
     HDDA_CUDA_TRY(cudaGetLastError());
   }
@@ -611,7 +679,7 @@ int update_vdb(hdda_grid* g, const uint8_t* dense, const int64_t* blocks, int64_
   cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);
   if (e != cudaSuccess) st = cuda_error(e, "cudaMemsetAsync");
   if (st == HDDA_OK) {
-    KernelTimer kt("update_vdb", s);  // the update's five kernels together
+    KernelTimer kt("update_vdb", s);  // the update's six kernels together
     vdb_update_blocks_kernel<<<blocks_for(count * 32, 256), 256, 0, s>>>(
         dense, g->L, g->R, g->B, blocks, count, g->blk_masks, g->blk_state, changed, flags,
         status);
@@ -626,6 +694,7 @@ int update_vdb(hdda_grid* g, const uint8_t* dense, const int64_t* blocks, int64_
     vdb_rewrite_leaves_kernel<<<blocks_for(count * 16, 256), 256, 0, s>>>(
         g->B, g->N, blocks, count, changed, flags, g->blk_state, g->blk_masks, g->child,
         g->prefix, g->leaves, g->lsub);
+    region_map_kernel<<<blocks_for(g->map_cells(), 256), 256, 0, s>>>(g->view(), g->rmap);
     kt.stop();
     e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_error(e, "update kernels");
@@ -685,6 +754,7 @@ extern "C" int hdda_grid_stats_get(const hdda_grid* g, hdda_grid_stats* out) {
   out->n_leaves = totals[0];
   out->n_tiles = totals[1];
   out->bytes = structure_bytes(g, totals[0]);
+  if (g->kind == HDDA_GRID_VDB) out->map_bytes = g->map_cells() * (int64_t)sizeof(uint16_t);
   return HDDA_OK;
 }
 
@@ -715,6 +785,9 @@ extern "C" int hdda_grid_copy_array(const hdda_grid* g, int which, void* dst, si
       break;
     case HDDA_ARRAY_NODE_SUPER:
       if (vdb) { src = g->nsuper; n = (size_t)g->nodes_total() * kSuperWords * 4; }
+      break;
+    case HDDA_ARRAY_REGION_MAP:
+      if (vdb) { src = g->rmap; n = (size_t)g->map_cells() * sizeof(uint16_t); }
       break;
     default: break;
   }

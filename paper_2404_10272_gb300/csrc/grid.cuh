@@ -23,7 +23,8 @@ struct hdda_grid {
   uint32_t* leaves = nullptr;    // vdb [L*B^3][16] capacity, compact prefix used
   uint32_t* nsuper = nullptr;    // vdb [L*N^3][kSuperWords] refinement masks
   uint32_t* lsub = nullptr;      // vdb [L*B^3][kLeafSubWords] capacity, per leaf
-  int refine = 1;                // HDDA uses the refinement masks
+  uint16_t* rmap = nullptr;      // vdb [L][C^3] region map, C = ceil(R / 2)
+  int refine = 1;                // HDDA walks the refined tree (through the region map)
   int walk_variant = HDDA_WALK_BRANCH;  // control flow of the two-pass walk
   // build temporaries (kept so that a rebuild allocates nothing)
   uint32_t* blk_masks = nullptr; // [L*B^3][16]
@@ -38,6 +39,10 @@ struct hdda_grid {
   int64_t nodes_total() const { return (int64_t)L * N * N * N; }
   int64_t blocks_total() const { return (int64_t)L * B * B * B; }
   int64_t thr_count() const { return (int64_t)L * 3 * (R + 1); }
+  int64_t map_cells() const {
+    const int64_t C = (R + 1) / 2;
+    return (int64_t)L * C * C * C;
+  }
 
   hdda::GridDev view() const {
     hdda::GridDev g{};
@@ -52,7 +57,7 @@ struct hdda_grid {
     }
     g.thr = thr; g.bits = bits; g.child = child; g.tile = tile;
     g.prefix = prefix; g.nstate = nstate; g.leaves = leaves;
-    g.nsuper = nsuper; g.lsub = lsub;
+    g.nsuper = nsuper; g.lsub = lsub; g.rmap = rmap;
     g.check = hdda::region_checks_on() ? 1 : 0;
     return g;
   }

@@ -28,9 +28,19 @@ constexpr int kLeafWords = 512 / 32;            // 16 words per leaf
 //   for the 2^3-voxel cells that are fully occupied.
 constexpr int kSuperWords = 2 + 16;
 constexpr int kLeafSubWords = 5;
+// Region map (built from the refined tree): one 16-bit entry per 2^3-voxel
+// cell, level by level, cells in C order over C = ceil(R / 2) per axis.
+// Bits 8-15: log2 of the edge of the coarsest uniform region of the refined
+// tree that holds the cell (0: the cell itself is not uniform; 1: a 2^3
+// cell; 2: an empty 4^3 cell; 3: an empty or tiled 8^3 block; 4, 5: an
+// empty 16^3 or 32^3 group; 7: an empty or full 128^3 node).  Bits 0-7: the
+// cell's voxels, bit ((x & 1) * 2 + (y & 1)) * 2 + (z & 1); 0x00 or 0xff
+// when the region is uniform, so the occupancy of any voxel is one bit test.
+constexpr int kMapNodeLog2 = 7;  // log2(kNodeVox)
 
 // Walk variants: dense bit array, VDB tree, VDB tree with refinement masks.
-enum WalkMode : int { kModeDense = 0, kModeVdb = 1, kModeVdbRefined = 2 };
+// kModeVdbMap walks the refined tree's regions, found through the region map.
+enum WalkMode : int { kModeDense = 0, kModeVdb = 1, kModeVdbMap = 2 };
 
 enum NodeState : uint32_t { kNodeEmpty = 0, kNodeMixed = 1, kNodeFull = 2 };
 enum BlockState : uint8_t { kBlockEmpty = 0, kBlockPartial = 1, kBlockFull = 2 };
@@ -67,6 +77,7 @@ struct GridDev {
   const uint32_t* leaves;    // vdb: [n_leaves][16]
   const uint32_t* nsuper;    // vdb: [L*N^3][kSuperWords]
   const uint32_t* lsub;      // vdb: [n_leaves][kLeafSubWords]
+  const uint16_t* rmap;      // vdb: [L][C][C][C] region map, C = ceil(R / 2)
   int check;                 // walk checks that each region holds its point
 };
 

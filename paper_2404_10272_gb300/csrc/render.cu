@@ -298,7 +298,7 @@ int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* 
     const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
     const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, skip, s)
                    : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, skip, s)
-                                      : launch_walk_mode<kModeVdbRefined>(w, stage, skip, s);
+                                      : launch_walk_mode<kModeVdbMap>(w, stage, skip, s);
     if (st != HDDA_OK) return st;
   }
   {
@@ -317,7 +317,7 @@ int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* 
             ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, StoreArgs{});
         break;
       default:
-        render_kernel<kModeVdbRefined, false><<<nb, kRenderWarps * 32, fsm, s>>>(
+        render_kernel<kModeVdbMap, false><<<nb, kRenderWarps * 32, fsm, s>>>(
             ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, StoreArgs{});
         break;
     }
@@ -368,7 +368,7 @@ int launch_sample_composite(const float* ro, const float* rd, int64_t n, const h
     const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
     const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, skip, s)
                    : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, skip, s)
-                                      : launch_walk_mode<kModeVdbRefined>(w, stage, skip, s);
+                                      : launch_walk_mode<kModeVdbMap>(w, stage, skip, s);
     if (st != HDDA_OK) return st;
   }
   {
@@ -397,7 +397,7 @@ int launch_sample_composite(const float* ro, const float* rd, int64_t n, const h
             ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, out);
         break;
       default:
-        render_kernel<kModeVdbRefined, true><<<nb, kRenderWarps * 32, fsm, s>>>(
+        render_kernel<kModeVdbMap, true><<<nb, kRenderWarps * 32, fsm, s>>>(
             ro, rd, n, w.g, lat, nr, runs, field, G, rgba, ev, out);
         break;
     }

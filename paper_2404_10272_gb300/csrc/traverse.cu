@@ -13,7 +13,9 @@
 //            is the coarsest uniform node of the tree: an empty or full
 //            16^3-block node, an empty 32^3 or 16^3 group (refinement), an
 //            empty or tiled 8^3 block, an empty 4^3 cell, an empty or fully
-//            occupied 2^3 cell (refinement), or a voxel of a leaf.  Outside
+//            occupied 2^3 cell (refinement), or a voxel of a leaf; with the
+//            refinement, one load from the region map (grid.cu) names it,
+//            without the tree is descended per region.  Outside
 //            every cascade box the region is a half-space the ray is leaving
 //            towards, or everything when it never comes back.
 //   cross    the first later lattice point outside the region.  The ray's
@@ -551,7 +553,7 @@ int run_onepass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
                                                   capacity, state, counter, status, total);
       break;
     default:
-      onepass_kernel<kModeVdbRefined><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0,
+      onepass_kernel<kModeVdbMap><<<nb, kBS, 0, s>>>(ro, rd, n, g, lat, offsets, ray_idx, t0,
                                                          t1, capacity, state, counter, status,
                                                          total);
       break;
@@ -610,7 +612,7 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
     const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
     const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, skip, s)
                    : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, skip, s)
-                                      : launch_walk_mode<kModeVdbRefined>(w, stage, skip, s);
+                                      : launch_walk_mode<kModeVdbMap>(w, stage, skip, s);
     if (st != HDDA_OK) return st;
   }
   {
@@ -638,7 +640,7 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
             capacity, vec, emit_counter, status);
         break;
       default:
-        emit_kernel<kModeVdbRefined><<<emit_grid<kModeVdbRefined>(T), kEmitWarps * 32, 0, s>>>(
+        emit_kernel<kModeVdbMap><<<emit_grid<kModeVdbMap>(T), kEmitWarps * 32, 0, s>>>(
             ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
             capacity, vec, emit_counter, status);
         break;

@@ -89,11 +89,10 @@ struct Tabs {
   const uint32_t* tile;
   const uint32_t* prefix;
   const uint32_t* nstate;
-  const uint32_t* nsuper;
 };
 
 __device__ __forceinline__ Tabs global_tabs(const GridDev& g) {
-  return Tabs{g.thr, g.child, g.tile, g.prefix, g.nstate, g.nsuper};
+  return Tabs{g.thr, g.child, g.tile, g.prefix, g.nstate};
 }
 
 // x = o + tm * d per axis, one rounding per operation.
@@ -200,8 +199,18 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
       occ = (w >> (lin & 31)) & 1u;
       break;
     }
-    // node level: L * N^3 <= 8 * 8^3 nodes and L * B^3 * 16 <= 2^28 leaf words, so
-    // every offset below fits 32 bits (cheaper address arithmetic than 64-bit)
+    if constexpr (kMode == kModeVdbMap) {
+      // the refined tree's region, flattened: one 2-byte load.  C^3 * L <= 2^27 * 8
+      // entries, so the offset fits 32 bits
+      const int C = (g.R + 1) >> 1;
+      const int cell = ((l * C + (i[0] >> 1)) * C + (i[1] >> 1)) * C + (i[2] >> 1);
+      const uint32_t m = __ldg(g.rmap + cell);
+      occ = (m >> (((i[0] & 1) << 2) | ((i[1] & 1) << 1) | (i[2] & 1))) & 1u;
+      sz = 1 << (m >> 8);
+      break;
+    }
+    // plain tree.  Node level: L * N^3 <= 8 * 8^3 nodes and L * B^3 * 16 <= 2^28 leaf
+    // words, so every offset below fits 32 bits (cheaper address arithmetic than 64-bit)
     const int N = g.N;
     const int ng = l * N * N * N + ((i[0] >> 7) * N + (i[1] >> 7)) * N + (i[2] >> 7);
     const uint32_t st = ld<kSm>(tb.nstate + ng);
@@ -209,22 +218,6 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
       sz = kNodeVox;
       occ = st == kNodeFull;
       break;
-    }
-    if constexpr (kMode == kModeVdbRefined) {
-      // empty 32^3 group, then empty 16^3 group of the node
-      const uint32_t* ns = tb.nsuper + ng * kSuperWords;
-      const int g4 = (((i[0] >> 5) & 3) * 4 + ((i[1] >> 5) & 3)) * 4 + ((i[2] >> 5) & 3);
-      if (!((ld<kSm>(ns + (g4 >> 5)) >> (g4 & 31)) & 1u)) {
-        sz = 32;
-        occ = false;
-        break;
-      }
-      const int g2 = (((i[0] >> 4) & 7) * 8 + ((i[1] >> 4) & 7)) * 8 + ((i[2] >> 4) & 7);
-      if (!((ld<kSm>(ns + 2 + (g2 >> 5)) >> (g2 & 31)) & 1u)) {
-        sz = 16;
-        occ = false;
-        break;
-      }
     }
     // block level: empty or tile
     const int cell = (((i[0] >> 3) & 15) * 16 + ((i[1] >> 3) & 15)) * 16 + ((i[2] >> 3) & 15);
@@ -238,24 +231,6 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
     }
     // voxel of a leaf
     const uint32_t leaf = ld<kSm>(tb.prefix + ng * kNodeWords + w) + __popc(cw & (bit - 1u));
-    if constexpr (kMode == kModeVdbRefined) {
-      // empty 4^3 cell, then an empty or fully occupied 2^3 cell of the leaf
-      const uint32_t* ls = g.lsub + leaf * (uint32_t)kLeafSubWords;
-      const int c4 = (((i[0] >> 2) & 1) * 2 + ((i[1] >> 2) & 1)) * 2 + ((i[2] >> 2) & 1);
-      if (!((__ldg(ls + 2) >> c4) & 1u)) {
-        sz = 4;
-        occ = false;
-        break;
-      }
-      const int c2 = (((i[0] >> 1) & 3) * 4 + ((i[1] >> 1) & 3)) * 4 + ((i[2] >> 1) & 3);
-      const bool c2_any = (__ldg(ls + (c2 >> 5)) >> (c2 & 31)) & 1u;
-      // an empty 2^3 cell, or a fully occupied one: one region either way
-      if (!c2_any || ((__ldg(ls + 3 + (c2 >> 5)) >> (c2 & 31)) & 1u)) {
-        sz = 2;
-        occ = c2_any;
-        break;
-      }
-    }
     const int v = ((i[0] & 7) * 8 + (i[1] & 7)) * 8 + (i[2] & 7);
     const uint32_t lw = __ldg(g.leaves + (leaf * (uint32_t)kLeafWords + (uint32_t)(v >> 5)));
     occ = (lw >> (v & 31)) & 1u;
@@ -634,7 +609,7 @@ constexpr int kWalkBS = 1024;
 
 // Shared-memory bytes that stage the walk's tables (0 = they do not fit).
 struct StageLayout {
-  size_t tm, kidx, thr, child, tile, prefix, nstate, nsuper, bytes;
+  size_t tm, kidx, thr, child, tile, prefix, nstate, bytes;
 };
 
 __host__ __device__ inline StageLayout stage_layout(int K, int L, int R, int64_t nodes, int mode) {
@@ -643,15 +618,12 @@ __host__ __device__ inline StageLayout stage_layout(int K, int L, int R, int64_t
   s.tm = o; o += sizeof(float) * (size_t)K;
   s.kidx = o; o += sizeof(int) * (size_t)(kKidxMax + 2);
   s.thr = o; o += sizeof(float) * (size_t)L * 3 * (R + 1);
-  s.child = s.tile = s.prefix = s.nstate = s.nsuper = o;
-  if (mode != kModeDense) {
+  s.child = s.tile = s.prefix = s.nstate = o;
+  if (mode == kModeVdb) {
     s.child = o; o += 4 * (size_t)nodes * kNodeWords;
     s.tile = o; o += 4 * (size_t)nodes * kNodeWords;
     s.prefix = o; o += 4 * (size_t)nodes * kNodeWords;
     s.nstate = o; o += 4 * (size_t)nodes;
-  }
-  if (mode == kModeVdbRefined) {
-    s.nsuper = o; o += 4 * (size_t)nodes * kSuperWords;
   }
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
@@ -689,7 +661,7 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     ls.tm = s_tm;
     ls.kidx = s_kidx;
     tb.thr = s_thr;
-    if constexpr (kMode != kModeDense) {
+    if constexpr (kMode == kModeVdb) {
       uint32_t* s_child = reinterpret_cast<uint32_t*>(smem + sl.child);
       uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + sl.tile);
       uint32_t* s_prefix = reinterpret_cast<uint32_t*>(smem + sl.prefix);
@@ -702,11 +674,6 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
       tb.tile = s_tile;
       tb.prefix = s_prefix;
       tb.nstate = s_nstate;
-    }
-    if constexpr (kMode == kModeVdbRefined) {
-      uint32_t* s_nsuper = reinterpret_cast<uint32_t*>(smem + sl.nsuper);
-      stage_copy(s_nsuper, g.nsuper, nodes * kSuperWords);
-      tb.nsuper = s_nsuper;
     }
     __syncthreads();
   }
@@ -741,7 +708,7 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
 // The walk a grid takes: dense DDA, or HDDA with or without refinement.
 int walk_mode(const hdda_grid* grid) {
   if (grid->kind == HDDA_GRID_DENSE) return kModeDense;
-  return grid->refine ? kModeVdbRefined : kModeVdb;
+  return grid->refine ? kModeVdbMap : kModeVdb;
 }
 
 struct WalkArgs {

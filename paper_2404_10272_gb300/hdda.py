@@ -22,7 +22,7 @@ ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_STEP_LIMIT, ERR_TIMEOUT, ERR_OOM, E
 GRID_DENSE, GRID_VDB = 0, 1
 WALK_BRANCH, WALK_SKIP = 0, 1
 (ARRAY_THRESHOLDS, ARRAY_DENSE_BITS, ARRAY_CHILD_MASK, ARRAY_TILE_MASK, ARRAY_LEAF_PREFIX,
- ARRAY_LEAVES, ARRAY_NODE_SUPER, ARRAY_LEAF_SUB) = range(8)
+ ARRAY_LEAVES, ARRAY_NODE_SUPER, ARRAY_LEAF_SUB, ARRAY_REGION_MAP) = range(9)
 
 EXPORTED = [
     "hdda_version", "hdda_last_error", "hdda_pack_dense", "hdda_build_vdb", "hdda_grid_rebuild",
@@ -73,7 +73,7 @@ class GridStats(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("levels", ctypes.c_int32), ("res", ctypes.c_int32),
                 ("blocks", ctypes.c_int32), ("nodes", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("n_leaves", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("bytes", ctypes.c_int64),
-                ("dense_bytes", ctypes.c_int64)]
+                ("dense_bytes", ctypes.c_int64), ("map_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -201,14 +201,15 @@ class Grid:
     def array(self, which: int) -> np.ndarray:
         need = ctypes.c_size_t(0)
         _check(load().hdda_grid_copy_array(self._h, which, None, 0, ctypes.byref(need)))
-        dt = np.float32 if which == ARRAY_THRESHOLDS else np.uint32
-        out = np.zeros(need.value // 4, dt)
+        dt = {ARRAY_THRESHOLDS: np.float32, ARRAY_REGION_MAP: np.uint16}.get(which, np.uint32)
+        out = np.zeros(need.value // np.dtype(dt).itemsize, dt)
         _check(load().hdda_grid_copy_array(self._h, which, out.ctypes.data_as(ctypes.c_void_p),
                                            out.nbytes, ctypes.byref(need)))
         return out
 
     def set_refine(self, on: bool):
-        """VDB grids: walk with (True, default) or without the refinement masks."""
+        """VDB grids: walk the refined tree through its region map (True, default) or the
+        plain tree (False)."""
         _check(load().hdda_grid_set_refine(self._h, 1 if on else 0))
 
     def set_walk(self, variant: int):

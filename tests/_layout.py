@@ -1,11 +1,13 @@
-"""White-box restatement of the library's refinement-mask layout (not collected
-by pytest).
+"""White-box restatement of the library's refinement-mask and region-map
+layouts (not collected by pytest).
 
-The refinement masks are this library's own acceleration structure (an
-octree-style subdivision inside VDB nodes and leaves), not a definition from
-the paper, so they live with the tests rather than in the oracle.  The masks
-are derived here with numpy from a tree built by ``oracle.build_vdb`` and the
-layout documented for HDDA_ARRAY_NODE_SUPER / HDDA_ARRAY_LEAF_SUB in
+The refinement masks and the region map are this library's own acceleration
+structures (an octree-style subdivision inside VDB nodes and leaves, and its
+flattening into one entry per 2^3 cell), not definitions from the paper, so
+they live with the tests rather than in the oracle.  The masks are derived
+here with numpy from a tree built by ``oracle.build_vdb``, the map directly
+from the dense occupancy, both in the layouts documented for
+HDDA_ARRAY_NODE_SUPER / HDDA_ARRAY_LEAF_SUB / HDDA_ARRAY_REGION_MAP in
 include/hdda.h, and compared word for word with what the library exports.
 """
 import numpy as np
@@ -42,3 +44,47 @@ def vdb_refinement(v: dict) -> tuple[np.ndarray, np.ndarray]:
     return nsuper.astype(np.uint32), lsub
 
 
+
+
+def region_map(occ: np.ndarray) -> np.ndarray:
+    """Region map of an occupancy grid uint8 [L, R, R, R], in the library's layout:
+    uint16 [L, C, C, C] with C = ceil(R / 2).  For each 2^3 cell, the high byte is log2 of
+    the edge of the first uniform region in the order 128^3 node (empty or full), 32^3
+    group (empty), 16^3 group (empty), 8^3 block (empty or full), 4^3 cell (empty), 2^3
+    cell (empty or full) -- aligned cubes of the grid padded with empty voxels -- and 0
+    when none is; the low byte holds the cell's voxels, bit ((x%2)*2 + y%2)*2 + z%2."""
+    L, R = occ.shape[0], occ.shape[1]
+    P = -(-R // 128) * 128
+    pad = np.zeros((L, P, P, P), bool)
+    pad[:, :R, :R, :R] = occ != 0
+    C = (R + 1) // 2
+
+    def cubes(s, fn):
+        n = P // s
+        return fn(pad.reshape(L, n, s, n, s, n, s), axis=(2, 4, 6))
+
+    def per_cell(a, s):
+        # value of the size-s cube holding each 2^3 cell, for the first C cells per axis
+        r = s // 2
+        return a.repeat(r, 1).repeat(r, 2).repeat(r, 3)[:, :C, :C, :C]
+
+    cells = pad.reshape(L, P // 2, 2, P // 2, 2, P // 2, 2).transpose(0, 1, 3, 5, 2, 4, 6)
+    cells = cells.reshape(L, P // 2, P // 2, P // 2, 8)[:, :C, :C, :C]
+    bits = (cells.astype(np.uint16) << np.arange(8, dtype=np.uint16)).sum(-1).astype(np.uint16)
+    out = np.zeros((L, C, C, C), np.uint16)
+    done = np.zeros((L, C, C, C), bool)
+
+    def take(mask, lg, full):
+        nonlocal done
+        m = mask & ~done
+        out[m] = (lg << 8) | (0xFF if full else 0)
+        done |= m
+
+    for s, lg, kinds in ((128, 7, (False, True)), (32, 5, (False,)), (16, 4, (False,)),
+                         (8, 3, (False, True)), (4, 2, (False,)), (2, 1, (False, True))):
+        empty = per_cell(~cubes(s, np.any), s)
+        full = per_cell(cubes(s, np.all), s)
+        for f in kinds:
+            take(full if f else empty, lg, f)
+    out[~done] = bits[~done]
+    return out

@@ -209,6 +209,9 @@ def test_grid_structures_match_oracle(H):
     nsuper, lsub = _layout.vdb_refinement(v)
     np.testing.assert_array_equal(gv.array(H.ARRAY_NODE_SUPER), nsuper.reshape(-1))
     np.testing.assert_array_equal(gv.array(H.ARRAY_LEAF_SUB), lsub.reshape(-1))
+    # region map (R = 37: odd, so the last cell per axis holds one voxel and padding)
+    np.testing.assert_array_equal(gv.array(H.ARRAY_REGION_MAP), _layout.region_map(occ).reshape(-1))
+    assert st.map_bytes == 3 * 19 ** 3 * 2
     # leaf prefix: global index of the first leaf of each child-mask word
     child = v["child"].reshape(-1)
     pc = np.array([bin(int(w)).count("1") for w in child])
@@ -247,6 +250,8 @@ def test_table3_sizes(H):
                         + 18 * 4 + 20 * v["n_leaves"])
     gv.set_refine(False)
     assert gv.stats().bytes == 36 + 3 * 129 * 4 + (3 * 128 * 4 + 4) + 64 * v["n_leaves"]
+    # the region map beside it: 2 bytes per 2^3 cell, twice the dense bit array
+    assert st.map_bytes == 2 * 64 ** 3 == 2 * gd.stats().dense_bytes
 
 
 def test_rebuild_matches_fresh_build(H):

@@ -1,7 +1,7 @@
 """Incremental rebuild (hdda_grid_update): after an update with the list of
 8^3 blocks that may have changed, every array of the grid equals a fresh
 build from the new occupancy, bit for bit, and traversal stays equal to the
-oracle.  Covered: changes within partial leaves only (leaves rewritten in
+oracle.  The region map is among the arrays compared.  Covered: changes within partial leaves only (leaves rewritten in
 place), changes of block state (empty / partial / full: structure rebuilt),
 duplicates and unchanged blocks in the list, the all-blocks form, cascades,
 dense grids, and indices outside the grid."""
@@ -15,7 +15,7 @@ from _helpers import assert_same, gpu_samples, oracle_samples
 pytestmark = pytest.mark.gpu
 
 ARRAYS = ("ARRAY_CHILD_MASK", "ARRAY_TILE_MASK", "ARRAY_LEAF_PREFIX", "ARRAY_LEAVES",
-          "ARRAY_NODE_SUPER", "ARRAY_LEAF_SUB")
+          "ARRAY_NODE_SUPER", "ARRAY_LEAF_SUB", "ARRAY_REGION_MAP")
 
 
 @pytest.fixture(scope="module")
