@@ -88,6 +88,8 @@ def parse_args():
                          "object-centric, batch and serve summaries); batch: 64 mixed jobs in one "
                          "graph launch against 64 separate launches; serve: continuous-batching "
                          "render server under Poisson load")
+    ap.add_argument("--sampler-form", choices=["separate", "fused"], default="separate",
+                    help="with --profile-step: the two-pass samplers' form")
     ap.add_argument("--profile-step", choices=["hdda", "dense", "render"], default=None,
                     help="profiling aid: one count-only call, one warm-up step and one step of "
                          "the given path on camera 0, no timing, no JSON line")
@@ -214,7 +216,7 @@ def object_summary(d: dict) -> dict:
     """The object-centric frame's figures for the headline line's `object` key."""
     keep = ("ms_per_step", "value", "samples_per_step", "hdda_sampler", "dense_dda_sampler",
             "hdda_vs_dense_sampler_speedup", "roofline", "roofline_sampler", "render_only_step",
-            "dense_dda_step", "grid", "candidates_per_ray")
+            "dense_dda_step", "grid", "candidates_per_ray", "fused_sampler_form")
     out = {"workload": d["config"]["workload"], "rays_per_step": d["config"]["rays_per_step"],
            "steps": d["steps"], "rays_per_s": d["value"]}
     out.update({k: d[k] for k in keep if k in d and k != "value"})
@@ -371,11 +373,21 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
     # breakdown comes from a second, profiled pass over the same steps
     ms, samples, _, _ = timed(step_hdda, K, W)
     ms_prof, _, kern, _ = timed(step_hdda, K, 2, profile=True)
-    K2 = max(3, K // 2)
+    # the comparison loops run as many steps as the headline loop, so that they cover the
+    # same cameras (with K = 20, each camera once): the unbounded cameras differ in cost
+    K2 = K
     ms_dense, samples_dense, kern_dense, _ = timed(step_dense, K2, 2, profile=True)
     ms_sh, samp_sh, _, _ = timed(sampler_hdda, K, 2)
     ms_sd, samp_sd, _, _ = timed(sampler_dense, K2, 2)
     ms_r, _, kern_r, _ = timed(render_step, K, 2, profile=True)
+    # the same step and sampler with the walk and the emit fused into one kernel
+    hdda.set_sampler_form(hdda.SAMPLER_FUSED)
+    try:
+        # K steps: every camera once, as in the loops it is compared with
+        ms_fu, _, kern_fu, _ = timed(step_hdda, K, 2, profile=True)
+        ms_fu_s, _, _, _ = timed(sampler_hdda, K, 2)
+    finally:
+        hdda.set_sampler_form(hdda.SAMPLER_SEPARATE)
     ms_sync = ms_sp = ms_ss = ms_ds = ms_f = None
     kern_f = {}
     if full:
@@ -564,6 +576,7 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
     # and samples out, grid once.
     sampler_bytes = 24 * n + 8 * (n + 1) + 12 * S_avg + grid_bytes
     alg_bytes = {
+        "hdda_walk_emit": sampler_bytes,
         "hdda_walk": 24 * n + grid_bytes,
         "hdda_emit": 8 * (n + 1) + 12 * S_avg,
         "build_vdb": sc.occ.size + grid_bytes,
@@ -604,8 +617,9 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
 
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
     roofline = roof(dom) if dom else None
-    # the sampler as a whole (walk + emit): rays in, CSR offsets and samples out
-    sam_k = ("hdda_walk", "tile_scan", "hdda_emit")
+    # the sampler as a whole (walk + emit, or one walk-and-emit kernel): rays in, CSR
+    # offsets and samples out
+    sam_k = ("hdda_walk_emit",) if "hdda_walk_emit" in kern else ("hdda_walk", "hdda_emit")
     sam_ms = sum(kern[k][1] / max(1, kern[k][0]) for k in sam_k if k in kern)
     roofline_sampler = None
     if sam_ms > 0:
@@ -636,7 +650,7 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "rays_per_step": n,
                    "occupancy": [round(float(sc.occ[l].mean()), 4) for l in range(sc.levels)],
-                   "step": "vdb rebuild + hdda count/scan/emit (stream-ordered) + composite",
+                   "step": "vdb rebuild + hdda walk and emit (stream-ordered) + composite",
                    "l2": "flushed between steps (256 MiB write), flush outside timed windows",
                    "parallelism": f"replicas x{world}"},
         "samples_per_s": round(samples * world / (ms / 1e3), 1),
@@ -671,6 +685,14 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
             "render_fp32_tops": (round(render_evals * COMPOSITE_FP32_PER_BLOB
                                      / (kern_r["hdda_render"][1] / kern_r["hdda_render"][0] / 1e3)
                                      / 1e12, 2) if "hdda_render" in kern_r else None)},
+        "fused_sampler_form": {
+            "note": "the same step and sampler with the walk and the emit in one persistent "
+                    "kernel (hdda_set_sampler_form(HDDA_SAMPLER_FUSED)); same samples",
+            "step_ms": round(ms_fu / K, 4),
+            "sampler_ms_per_frame": round(ms_fu_s / K, 4),
+            "speedup_vs_separate": round(ms_sh / ms_fu_s, 3),
+            "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}
+                        for k, v in kern_fu.items()}},
         "hdda_vs_dense_sampler_speedup": round(ms_sd / K2 / (ms_sh / K), 3),
         "grid": {"vdb_bytes": grid_bytes, "vdb_plain_bytes": plain_bytes,
                  "dense_bytes": int(vstats.dense_bytes),
@@ -858,6 +880,8 @@ def profile_step(args):
     p = sc.params
     prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
     vdb = args.profile_step in ("hdda", "render")
+    hdda.set_sampler_form(hdda.SAMPLER_FUSED if args.sampler_form == "fused"
+                          else hdda.SAMPLER_SEPARATE)
     grid = hdda.build_vdb(dense, sc.aabbs) if vdb else hdda.pack_dense(dense, sc.aabbs)
     trav = hdda.traverse_hdda if vdb else hdda.traverse_dense
     rgba = torch.empty((o.shape[0], 4), dtype=torch.float32, device="cuda")

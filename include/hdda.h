@@ -153,8 +153,8 @@ typedef enum {
        entry per 2^3-voxel cell (voxel_c / 2 per axis).  Bits 8-15: log2 of
        the edge of the coarsest uniform region of the refined tree holding
        the cell: 7 = an empty or full 128^3 node, 5 / 4 = an empty 32^3 /
-       16^3 group, 3 = an empty or tiled 8^3 block, 2 = an empty 4^3 cell,
-       1 = an empty or full 2^3 cell, 0 = the cell is not uniform.  Bits 0-7:
+       16^3 group, 3 = an empty or tiled 8^3 block, 2 = an empty or full 4^3
+       cell, 1 = an empty or full 2^3 cell, 0 = the cell is not uniform.  Bits 0-7:
        voxel (x, y, z) of the cell is bit ((x%2)*2 + y%2)*2 + z%2; all eight
        equal (0x00 or 0xff) when the region is uniform.                       */
     HDDA_ARRAY_REGION_MAP = 8
@@ -243,7 +243,7 @@ int hdda_grid_copy_array(const hdda_grid* grid, int which, void* dst, size_t byt
  * Chooses the hierarchy hdda_traverse_hdda walks on a VDB grid.  on = 1 (the
  * default): besides empty nodes, empty or tiled 8^3 blocks and single leaf
  * voxels, it also crosses empty 32^3 and 16^3 groups inside a node and
- * empty 4^3 and empty or full 2^3 cells inside a leaf in one step each, an
+ * empty or full 4^3 and 2^3 cells inside a leaf in one step each, an
  * octree-style refinement of the VDB tree (Sec. 5 names finer subdivision
  * as worth studying).  The walk finds each region in the region map
  * (HDDA_ARRAY_REGION_MAP, built with the tree) by one lookup.  on = 0: the
@@ -547,6 +547,28 @@ int hdda_profiler_read(hdda_kernel_time* out, int cap, int* n_out);
  */
 int hdda_set_region_checks(int on);
 int hdda_region_checks(void);
+
+/*
+ * Form of the two-pass samplers (hdda_traverse_dense, hdda_traverse_hdda,
+ * hdda_traverse_async); the samples are the same in both.
+ *   HDDA_SAMPLER_SEPARATE (default): the walk (pass 1), a scan of the
+ *     per-tile sample totals (the prefix sum of Algorithm 1's per-ray sample
+ *     counts, for the output offsets) and the emit (pass 2) as three kernels.
+ *   HDDA_SAMPLER_FUSED: one persistent kernel; its warps walk 32-ray tiles
+ *     until none is left, then write tiles out in order, each tile's offset
+ *     from a decoupled look-back over the totals the walks published, so
+ *     that warps done walking write out early tiles while the last ones are
+ *     still walked.
+ *     On full frames it measured no faster than the separate form (the
+ *     write-out's memory waits slow the walks that share its SMs).
+ * Not in the paper (its sampler is one thread per ray appending to a
+ * buffer).  The setting is process-wide and read when a call enqueues its
+ * work.  hdda_set_sampler_form returns HDDA_OK, or HDDA_ERR_INVALID_ARG for
+ * any other value; hdda_sampler_form returns the current form.
+ */
+typedef enum { HDDA_SAMPLER_SEPARATE = 0, HDDA_SAMPLER_FUSED = 1 } hdda_sampler_form_t;
+int hdda_set_sampler_form(int form);
+int hdda_sampler_form(void);
 
 #ifdef __cplusplus
 }

@@ -424,9 +424,9 @@ __global__ void vdb_rewrite_leaves_kernel(int B, int N, const int64_t* __restric
 // The region map (layout in hdda_internal.cuh), written after the tree and
 // its refinement masks.  Each thread descends the refined tree from the
 // cell's first voxel, exactly as a walk over the tree would: node state,
-// empty 32^3 and 16^3 groups, empty or tiled 8^3 block, empty 4^3 cell,
-// empty or full 2^3 cell; a cell that is none of these keeps its 8 voxel
-// bits.  Voxels past the grid edge (odd R) are empty in the leaves.
+// empty 32^3 and 16^3 groups, empty or tiled 8^3 block, empty or full 4^3
+// cell (full: its eight 2^3 cells are), empty or full 2^3 cell; a cell that
+// is none of these keeps its 8 voxel bits.  Voxels past the grid edge (odd R) are empty in the leaves.
 __global__ void region_map_kernel(GridDev g, uint16_t* __restrict__ rmap) {
   const int C = (g.R + 1) >> 1;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -467,6 +467,11 @@ __global__ void region_map_kernel(GridDev g, uint16_t* __restrict__ rmap) {
     const uint32_t* ls = g.lsub + leaf * (uint32_t)kLeafSubWords;
     const int c4 = (((i[0] >> 2) & 1) * 2 + ((i[1] >> 2) & 1)) * 2 + ((i[2] >> 2) & 1);
     if (!((ls[2] >> c4) & 1u)) { lg = 2; break; }
+    // a 4^3 cell is full when its eight 2^3 cells are: bits base + {0, 1, 4, 5, 16, 17,
+    // 20, 21} of the leaf's 64-bit full-cell mask
+    const uint64_t full2 = (uint64_t)ls[3] | ((uint64_t)ls[4] << 32);
+    const int base4 = 32 * ((i[0] >> 2) & 1) + 8 * ((i[1] >> 2) & 1) + 2 * ((i[2] >> 2) & 1);
+    if (((full2 >> base4) & 0x330033ull) == 0x330033ull) { lg = 2; mask = 0xffu; break; }
     const int c2 = (((i[0] >> 1) & 3) * 4 + ((i[1] >> 1) & 3)) * 4 + ((i[2] >> 1) & 3);
     lg = 1;
     if (!((ls[c2 >> 5] >> (c2 & 31)) & 1u)) break;          // empty 2^3 cell

@@ -32,7 +32,7 @@ constexpr int kLeafSubWords = 5;
 // cell, level by level, cells in C order over C = ceil(R / 2) per axis.
 // Bits 8-15: log2 of the edge of the coarsest uniform region of the refined
 // tree that holds the cell (0: the cell itself is not uniform; 1: a 2^3
-// cell; 2: an empty 4^3 cell; 3: an empty or tiled 8^3 block; 4, 5: an
+// cell; 2: an empty or full 4^3 cell; 3: an empty or tiled 8^3 block; 4, 5: an
 // empty 16^3 or 32^3 group; 7: an empty or full 128^3 node).  Bits 0-7: the
 // cell's voxels, bit ((x & 1) * 2 + (y & 1)) * 2 + (z & 1); 0x00 or 0xff
 // when the region is uniform, so the occupancy of any voxel is one bit test.
@@ -134,6 +134,8 @@ bool profiler_on();
 bool counters_on();
 // True while the walk's device-side region checks are enabled (runtime.cu).
 bool region_checks_on();
+// The two-pass samplers' current form, HDDA_SAMPLER_FUSED or _SEPARATE (runtime.cu).
+int sampler_form();
 // Blob evaluations counted by the compositor since the last call (composite.cu).
 unsigned long long composite_take_blob_evals();
 // The same count for the render-only path (render.cu).

@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32, 6) render_kernel(
         ray.o[c] = o[c];
         ray.d[c] = d[c];
         ray.neg[c] = d[c] < 0.f;
-        ray.inv[c] = 1.0f / d[c];
+        ray.inv[c] = d[c] != 0.f ? 1.0f / d[c] : INFINITY;
       }
       k_next = walk_from<kMode, false>(g, global_tabs(g), lat, h, ray, k_next, sr + lane,
                                        kRenderRays, nr);

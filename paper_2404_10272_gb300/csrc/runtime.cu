@@ -70,6 +70,12 @@ std::atomic<int> g_region_checks{0};
 
 bool region_checks_on() { return g_region_checks.load(std::memory_order_relaxed) != 0; }
 
+namespace {
+std::atomic<int> g_sampler_form{HDDA_SAMPLER_SEPARATE};
+}  // namespace
+
+int sampler_form() { return g_sampler_form.load(std::memory_order_relaxed); }
+
 KernelTimer::KernelTimer(const char* name, cudaStream_t s, bool allow) : name_(name), s_(s) {
   if (!allow) return;
   std::lock_guard<std::mutex> lock(g_prof_mu);
@@ -110,6 +116,16 @@ extern "C" int hdda_set_region_checks(int on) {
 }
 
 extern "C" int hdda_region_checks(void) { return hdda::region_checks_on() ? 1 : 0; }
+
+extern "C" int hdda_set_sampler_form(int form) {
+  if (form != HDDA_SAMPLER_FUSED && form != HDDA_SAMPLER_SEPARATE)
+    return hdda::set_error(HDDA_ERR_INVALID_ARG, "sampler form %d is neither separate (0) "
+                           "nor fused (1)", form);
+  hdda::g_sampler_form.store(form, std::memory_order_relaxed);
+  return HDDA_OK;
+}
+
+extern "C" int hdda_sampler_form(void) { return hdda::sampler_form(); }
 
 extern "C" int hdda_profiler_read(hdda_kernel_time* out, int cap, int* n_out) {
   using namespace hdda;

@@ -12,10 +12,10 @@
 //            throughout.  For dense DDA the region is the voxel; for HDDA it
 //            is the coarsest uniform node of the tree: an empty or full
 //            16^3-block node, an empty 32^3 or 16^3 group (refinement), an
-//            empty or tiled 8^3 block, an empty 4^3 cell, an empty or fully
-//            occupied 2^3 cell (refinement), or a voxel of a leaf; with the
-//            refinement, one load from the region map (grid.cu) names it,
-//            without the tree is descended per region.  Outside
+//            empty or tiled 8^3 block, an empty or fully occupied 4^3 or 2^3
+//            cell (refinement), or a voxel of a leaf; with the refinement,
+//            one load from the region map (grid.cu) names it, without the
+//            tree is descended per region.  Outside
 //            every cascade box the region is a half-space the ray is leaving
 //            towards, or everything when it never comes back.
 //   cross    the first later lattice point outside the region.  The ray's
@@ -162,9 +162,12 @@ __device__ __forceinline__ int64_t cta_exclusive_scan64(int64_t v, int64_t* tota
 // decoupled look-back over tiles
 // ---------------------------------------------------------------------------
 
+// State words: the top two bits flag the value as the tile's own sample
+// total (its aggregate) or as its inclusive prefix.
 constexpr unsigned long long kFlagAggregate = 1ull << 62;
 constexpr unsigned long long kFlagPrefix = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
   unsigned long long v;
@@ -176,21 +179,31 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Publishes this tile's aggregate, sums the predecessors back to the first
-// published prefix, publishes the inclusive prefix and returns the
+// True (on every lane) once some wait of the launch has run out of polls:
+// checked every 1024 polls, so that after one timeout the other waits end
+// at once instead of each running out in turn.
+__device__ __forceinline__ bool gave_up(const unsigned* status, unsigned polls) {
+  if (polls & 1023u) return false;
+  unsigned v = 0;
+  if ((threadIdx.x & 31) == 0) v = *reinterpret_cast<const volatile unsigned*>(status);
+  return (__shfl_sync(kFull, v, 0) & kDevTimeout) != 0;
+}
+
+// Sums the aggregates of the tiles before `tile` back to the first published
+// prefix, publishes the inclusive prefix (excl + agg) and returns the
 // exclusive one.  Called by one whole warp, which reads 32 predecessors per
-// poll.  Every predecessor tile was handed out earlier and is running or
-// done, so each wait ends; the poll count is still bounded, and running out
-// of it raises kDevTimeout (the host then reports HDDA_ERR_TIMEOUT) and
-// publishes what it has so that later tiles finish.
-__device__ int64_t lookback(unsigned long long* state, int tile, int64_t agg,
-                            unsigned* status) {
+// poll, once the tile's own aggregate is published.  Every predecessor tile
+// was handed out earlier and publishes its aggregate without waiting for
+// any other tile, so each wait ends; the poll count is still bounded, and
+// running out of it raises kDevTimeout (the host then reports
+// HDDA_ERR_TIMEOUT) and publishes what it has so that later tiles finish.
+__device__ int64_t lookback_prefix(unsigned long long* state, int tile, int64_t agg,
+                                   unsigned* status) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
     if (lane == 0) st_release(state, kFlagPrefix | (unsigned long long)agg);
     return 0;
   }
-  if (lane == 0) st_release(state + tile, kFlagAggregate | (unsigned long long)agg);
   int64_t excl = 0;
   int base = tile - 1;  // lane i looks at tile base - i
   unsigned polls = 0;
@@ -203,7 +216,7 @@ __device__ int64_t lookback(unsigned long long* state, int tile, int64_t agg,
     const int first_p = pmask ? __ffs(pmask) - 1 : 32;  // nearest published prefix
     const unsigned need = first_p >= 31 ? kFull : ((2u << first_p) - 1u);
     if (zmask & need) {  // a tile this one depends on has not published yet
-      if (++polls > kSpinLimit) {
+      if (++polls > kSpinLimit || gave_up(status, polls)) {
         if (lane == 0) atomicOr(status, kDevTimeout);
         break;
       }
@@ -219,6 +232,30 @@ __device__ int64_t lookback(unsigned long long* state, int tile, int64_t agg,
   }
   if (lane == 0) st_release(state + tile, kFlagPrefix | (unsigned long long)(excl + agg));
   return excl;
+}
+
+// Publishes this tile's aggregate, then looks back (lookback_prefix).
+__device__ int64_t lookback(unsigned long long* state, int tile, int64_t agg,
+                            unsigned* status) {
+  if (tile != 0 && (threadIdx.x & 31) == 0)
+    st_release(state + tile, kFlagAggregate | (unsigned long long)agg);
+  return lookback_prefix(state, tile, agg, status);
+}
+
+// Waits (bounded, as lookback_prefix) until the tile's aggregate is
+// published and returns it.  Every lane acquires the word itself, so the
+// tile's counts and runs, stored before the release, are visible to each.
+__device__ int64_t wait_aggregate(const unsigned long long* state, int tile, unsigned* status) {
+  unsigned polls = 0;
+  for (;;) {
+    const unsigned long long w = ld_acquire(state + tile);
+    if (__all_sync(kFull, (w & ~kValueMask) != 0)) return (int64_t)(w & kValueMask);
+    if (++polls > kSpinLimit || gave_up(status, polls)) {
+      if ((threadIdx.x & 31) == 0) atomicOr(status, kDevTimeout);
+      return 0;
+    }
+    __nanosleep(64);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -286,65 +323,57 @@ __global__ void __launch_bounds__(kBS) onepass_kernel(
 constexpr int kEmitWarps = 4;
 
 // Pass 2 for one 32-ray tile, independent of every other tile: its offset
-// is the tile's prefix plus a warp scan; its runs go to shared memory
-// (my_runs: run j of lane i at [j * 32 + i]; my_end: end position of lane
-// i's samples) and are expanded into samples.
+// is the tile's prefix plus a warp scan; its runs become a record list in
+// shared memory (rec: kRecMax records and a sentinel) that expand_records
+// turns into samples.  A ray with more runs than were kept walks again.
 template <int kMode>
 __device__ __forceinline__ void emit_tile(
-    int64_t tile, uint2* my_runs, int64_t* my_end, const float* __restrict__ ro,
-    const float* __restrict__ rd, int64_t n, const GridDev& g, const LatticeDev& lat,
-    const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
-    const uint2* __restrict__ runs, const int64_t* __restrict__ tile_prefix,
-    int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
-    float* __restrict__ t1, int64_t capacity, bool vec, unsigned* __restrict__ status) {
+    int64_t tile, uint2* rec, const float* __restrict__ ro, const float* __restrict__ rd,
+    int64_t n, const GridDev& g, const LatticeDev& lat, const int32_t* __restrict__ counts,
+    const uint8_t* __restrict__ nruns, const uint2* __restrict__ runs,
+    const int64_t* __restrict__ tile_prefix, int64_t* __restrict__ offsets,
+    int32_t* __restrict__ ray_idx, float* __restrict__ t0, float* __restrict__ t1,
+    int64_t capacity, bool vec, unsigned* __restrict__ status) {
   const int lane = threadIdx.x & 31;
   const int64_t r = tile * 32 + lane;
-  const int64_t c = r < n ? (int64_t)counts[r] : 0;
+  const int c = r < n ? counts[r] : 0;
   const int nr = r < n ? (int)nruns[r] : 0;
-  if (capacity > 0) {
-    // four independent loads in flight per lane (the runs of one index j are
-    // contiguous over the warp's lanes)
-    const int kept = min(nr, kMaxRuns);
-    for (int j0 = 0; __any_sync(kFull, j0 < kept); j0 += 4) {
-      uint2 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (j0 + u < kept) v[u] = __ldg(runs + (int64_t)(j0 + u) * n + r);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (j0 + u < kept) my_runs[(j0 + u) * 32 + lane] = v[u];
-    }
-    __syncwarp();
-  }
-  int64_t inc = c;
+  const int64_t wbeg = __ldg(tile_prefix + tile);
+  // a tile holds at most 32 * 2^24 samples: 32-bit positions within it
+  int inc = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(kFull, inc, o);
+    const int y = __shfl_up_sync(kFull, inc, o);
     if (lane >= o) inc += y;
   }
-  const int64_t off = __ldg(tile_prefix + tile) + inc - c;
+  const int q = inc - c;
+  const int tot = __shfl_sync(kFull, inc, 31);
+  const int64_t off = wbeg + q;
   if (capacity > 0) {
     // with too small a buffer the CSR offsets are clamped to it, so that a
     // consumer of the arrays stays in bounds; the status says what happened
     if (r < n) offsets[r] = min(off, capacity);
     if (r == n - 1) offsets[n] = min(off + c, capacity);
-    if (__shfl_sync(kFull, off + c, 31) > capacity && lane == 0) atomicOr(status, kDevCapacity);
+    if (wbeg + tot > capacity && lane == 0) atomicOr(status, kDevCapacity);
   } else {
     if (r < n) offsets[r] = off;
     return;
   }
-  const bool overflow = nr > kMaxRuns;
-  if (vec) {
-    my_end[lane] = off + c;
-    runs_to_positions(my_runs, lane, min(nr, kMaxRuns), off, __shfl_sync(kFull, off, 0));
-    __syncwarp();
-    expand_warp_v4(off, c, overflow, my_runs, (int32_t)(tile * 32), my_end, lat.t, capacity,
-                   ray_idx, t0, t1);
-  } else {
-    expand_warp<true>(off, c, overflow, my_runs, 32, (int32_t)(tile * 32), lat.t, capacity,
-                      ray_idx, t0, t1);
+  const int kept = c <= 0 ? 0 : nr > kMaxRuns ? 1 : nr;
+  int kinc = kept;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, kinc, o);
+    if (lane >= o) kinc += y;
   }
-  if (overflow) {
+  const int nrec = __shfl_sync(kFull, kinc, 31);
+  list_runs(rec, kinc - kept, lane, nr, c, (uint32_t)q, runs + r, n);
+  if (lane == 0) rec[nrec] = make_uint2(kRecEnd, 0u);
+  __syncwarp();
+  const int64_t room = capacity - wbeg;
+  const int lim = room <= 0 ? 0 : (int)min((int64_t)tot, room);
+  expand_records(rec, nrec, lim, wbeg, (int32_t)(tile * 32), lat.t, vec, ray_idx, t0, t1);
+  if (nr > kMaxRuns) {
     Ray ray;
     load_ray(ro, rd, r, ray);
     const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
@@ -358,15 +387,14 @@ __device__ __forceinline__ void emit_tile(
 // until none is left, so a warp that finishes early takes more tiles
 // instead of idling until its CTA's slowest tile is done.
 template <int kMode>
-__global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
+__global__ void __launch_bounds__(kEmitWarps * 32, 8) emit_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
     const uint2* __restrict__ runs, const int64_t* __restrict__ tile_prefix,
     int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
     float* __restrict__ t1, int64_t capacity, bool vec, unsigned* __restrict__ tile_counter,
     unsigned* __restrict__ status) {
-  __shared__ uint2 s_runs[kEmitWarps][kMaxRuns * 32];
-  __shared__ int64_t s_end[kEmitWarps][32];
+  __shared__ uint2 s_rec[kEmitWarps][kRecMax + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned T = (unsigned)((n + 31) / 32);
   for (;;) {
@@ -374,8 +402,8 @@ __global__ void __launch_bounds__(kEmitWarps * 32) emit_kernel(
     if (lane == 0) tile = atomicAdd(tile_counter, 1u);
     tile = __shfl_sync(kFull, tile, 0);
     if (tile >= T) break;
-    emit_tile<kMode>(tile, s_runs[warp], s_end[warp], ro, rd, n, g, lat, counts, nruns, runs,
-                     tile_prefix, offsets, ray_idx, t0, t1, capacity, vec, status);
+    emit_tile<kMode>(tile, s_rec[warp], ro, rd, n, g, lat, counts, nruns, runs, tile_prefix,
+                     offsets, ray_idx, t0, t1, capacity, vec, status);
     __syncwarp();  // the next tile reuses this warp's shared memory
   }
 }
@@ -393,6 +421,194 @@ unsigned emit_grid(int64_t T) {
   const int64_t want = (T + kEmitWarps - 1) / kEmitWarps;
   const int64_t full = (int64_t)(sms > 0 ? sms : 1) * per_sm;
   return (unsigned)(want < full ? want : full);
+}
+
+// ---------------------------------------------------------------------------
+// fused sampler: the walk and the emit in one persistent kernel
+// ---------------------------------------------------------------------------
+//
+// Phase 1: each warp walks 32-ray tiles (as walk_kernel: counts, run counts
+// and runs to global memory) and publishes each tile's sample total as its
+// aggregate in the decoupled look-back's state word.  Phase 2, once every
+// tile has been handed out: warps take tiles to write out, in tile order.
+// Writing out = waiting for the tile's aggregate, looking back for its
+// exclusive prefix, writing the CSR offsets and expanding the runs through a
+// per-warp record list in shared memory (expand_records).  Warps whose walks
+// end early thus write out the first tiles while the last ones are still
+// walked, and no scan or emit launch follows.
+//
+// No wait can last forever: a walk publishes its aggregate without waiting
+// for anything, every tile has been handed out to a running warp before
+// phase 2 begins anywhere, and the waits themselves are bounded
+// (kDevTimeout).
+
+// Shared memory of the fused kernel: the staged tables (kSm), then one
+// record list (kRecMax records and the sentinel) per warp.
+__host__ __device__ inline size_t walk_emit_smem(size_t stage_bytes) {
+  return stage_bytes + (size_t)(kWalkBS / 32) * (kRecMax + 1) * sizeof(uint2);
+}
+
+// Writes out tile e: its CSR offsets and, below `capacity`, its samples.
+template <int kMode, bool kSm>
+__device__ __forceinline__ void emit_fused_tile(
+    int e, uint2* rec, const float* __restrict__ ro, const float* __restrict__ rd, int64_t n,
+    unsigned T, const GridDev& g, const Tabs& tb, const LatticeDev& ls, const LatHdr& h,
+    const int32_t* counts, const uint8_t* nruns, const uint2* runs, unsigned long long* state,
+    int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
+    float* __restrict__ t1, int64_t capacity, bool vec, int64_t* __restrict__ total,
+    unsigned* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t agg = wait_aggregate(state, e, status);
+  const int64_t excl = lookback_prefix(state, e, agg, status);
+  const int64_t r = (int64_t)e * 32 + lane;
+  // written in this kernel by another warp: read through L2 (after the acquire)
+  const int c = r < n ? __ldcg(counts + r) : 0;
+  const int nr = r < n ? (int)__ldcg(nruns + r) : 0;
+  // a tile holds at most 32 * 2^24 samples: 32-bit positions within it
+  int inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const int q = inc - c;  // this ray's first position within the tile
+  const int tot = __shfl_sync(kFull, inc, 31);
+  const int64_t off = excl + q;
+  if (capacity > 0) {
+    // with too small a buffer the CSR offsets are clamped to it, so that a
+    // consumer of the arrays stays in bounds; the status says what happened
+    if (r < n) offsets[r] = min(off, capacity);
+    if (r == n - 1) offsets[n] = min(off + c, capacity);
+    if (excl + tot > capacity && lane == 0) atomicOr(status, kDevCapacity);
+  } else {
+    if (r < n) offsets[r] = off;
+    if (r == n - 1) offsets[n] = off + c;
+  }
+  if (e == (int)T - 1 && lane == 0) *total = excl + tot;
+  if (capacity <= 0) return;
+  // the record list: an exclusive scan of the lanes' record counts
+  const int kept = c <= 0 ? 0 : nr > kMaxRuns ? 1 : nr;
+  int kinc = kept;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, kinc, o);
+    if (lane >= o) kinc += y;
+  }
+  const int nrec = __shfl_sync(kFull, kinc, 31);
+  list_runs(rec, kinc - kept, lane, nr, c, (uint32_t)q, runs + r, n);
+  if (lane == 0) rec[nrec] = make_uint2(kRecEnd, 0u);
+  __syncwarp();
+  const int64_t room = capacity - excl;
+  const int lim = room <= 0 ? 0 : (int)min((int64_t)tot, room);
+  expand_records(rec, nrec, lim, excl, (int32_t)((int64_t)e * 32), ls.t, vec, ray_idx, t0, t1);
+  __syncwarp();  // the next tile reuses rec
+  if (nr > kMaxRuns) {
+    Ray ray;
+    load_ray(ro, rd, r, ray);
+    int unused = 0;
+    walk<kMode, true, kSm>(g, tb, ls, h, ray, nullptr, 0, unused, (int32_t)r, off, capacity,
+                           ray_idx, t0, t1, status);
+  }
+}
+
+template <int kMode, bool kSm, bool kSkip, bool kCheck>
+__global__ void __launch_bounds__(kWalkBS) walk_emit_kernel(
+    const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
+    LatticeDev lat, int32_t* counts, uint8_t* nruns_out, uint2* runs,
+    unsigned long long* state, unsigned* __restrict__ walk_counter,
+    unsigned* __restrict__ emit_counter, int64_t* __restrict__ offsets,
+    int32_t* __restrict__ ray_idx, float* __restrict__ t0, float* __restrict__ t1,
+    int64_t capacity, bool vec, int64_t* __restrict__ total, unsigned* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+  Tabs tb = global_tabs(g);
+  LatticeDev ls = lat;
+  size_t stage_bytes = 0;
+  if constexpr (kSm) {
+    const int64_t nodes = (int64_t)g.L * g.N * g.N * g.N;
+    stage_bytes = stage_layout(lat.K, g.L, g.R, nodes, kMode).bytes;
+    stage_walk_tables<kMode>(smem, g, lat, h, tb, ls);
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint2* rec = reinterpret_cast<uint2*>(smem + stage_bytes) + warp * (kRecMax + 1);
+  const unsigned T = (unsigned)((n + 31) / 32);
+  for (;;) {  // phase 1: walk tiles until none is left
+    unsigned tile = 0;
+    if (lane == 0) tile = atomicAdd(walk_counter, 1u);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= T) break;
+    const int64_t r = (int64_t)tile * 32 + lane;
+    int64_t c = 0;
+    if (r < n) {
+      Ray ray;
+      int nr = 0;
+      if (load_ray(ro, rd, r, ray))
+        c = walk<kMode, false, kSm, kSkip, kCheck>(g, tb, ls, h, ray, runs + r, n, nr, 0, 0, 0,
+                                                  nullptr, nullptr, nullptr, status);
+      counts[r] = (int32_t)c;
+      nruns_out[r] = (uint8_t)min(nr, 255);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    __syncwarp();  // orders every lane's counts and runs before lane 0's release
+    if (lane == 0) st_release(state + tile, kFlagAggregate | (unsigned long long)c);
+  }
+  for (;;) {  // phase 2: every tile is handed out; write tiles out in order
+    unsigned e = 0;
+    if (lane == 0) e = atomicAdd(emit_counter, 1u);
+    e = __shfl_sync(kFull, e, 0);
+    if (e >= T) break;
+    emit_fused_tile<kMode, kSm>((int)e, rec, ro, rd, n, T, g, tb, ls, h, counts, nruns_out, runs,
+                                state, offsets, ray_idx, t0, t1, capacity, vec, total, status);
+  }
+}
+
+template <int kMode, bool kSm, bool kSkip>
+int launch_walk_emit(const WalkArgs& w, size_t stage, unsigned long long* state,
+                     unsigned* emit_counter, int64_t* offsets, int32_t* ray_idx, float* t0,
+                     float* t1, int64_t capacity, bool vec, int64_t* total, cudaStream_t s) {
+  auto kern = w.g.check ? walk_emit_kernel<kMode, kSm, kSkip, true>
+                        : walk_emit_kernel<kMode, kSm, kSkip, false>;
+  const size_t smem = walk_emit_smem(kSm ? stage : 0);
+  HDDA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  HDDA_CUDA_TRY(cudaGetDevice(&dev));
+  HDDA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HDDA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkBS, smem));
+  if (per_sm <= 0) return set_error(HDDA_ERR_INTERNAL, "fused sampler does not fit an SM");
+  // as the walk: one resident wave, at most one CTA per eight 32-ray tiles
+  const int64_t want = ((w.n + 31) / 32 + 7) / 8;
+  const int64_t full = (int64_t)sms * per_sm;
+  const unsigned grid = (unsigned)(want < full ? want : full);
+  kern<<<grid, kWalkBS, smem, s>>>(w.ro, w.rd, w.n, w.g, w.lat, w.counts, w.nruns, w.runs, state,
+                                   w.counter, emit_counter, offsets, ray_idx, t0, t1, capacity,
+                                   vec, total, w.status);
+  HDDA_CUDA_TRY(cudaGetLastError());
+  return HDDA_OK;
+}
+
+template <int kMode>
+int launch_walk_emit_mode(const WalkArgs& w, size_t stage, bool skip, unsigned long long* state,
+                          unsigned* emit_counter, int64_t* offsets, int32_t* ray_idx, float* t0,
+                          float* t1, int64_t capacity, bool vec, int64_t* total,
+                          cudaStream_t s) {
+  const bool sm = stage <= kMaxStageBytes;
+  if (skip)
+    return sm ? launch_walk_emit<kMode, true, true>(w, stage, state, emit_counter, offsets,
+                                                   ray_idx, t0, t1, capacity, vec, total, s)
+              : launch_walk_emit<kMode, false, true>(w, stage, state, emit_counter, offsets,
+                                                    ray_idx, t0, t1, capacity, vec, total, s);
+  return sm ? launch_walk_emit<kMode, true, false>(w, stage, state, emit_counter, offsets,
+                                                  ray_idx, t0, t1, capacity, vec, total, s)
+            : launch_walk_emit<kMode, false, false>(w, stage, state, emit_counter, offsets,
+                                                   ray_idx, t0, t1, capacity, vec, total, s);
+}
+
+const char* walk_emit_name(int mode) {
+  return mode == kModeDense ? "dense_walk_emit"
+         : mode == kModeVdb ? "hdda_walk_emit_plain" : "hdda_walk_emit";
 }
 
 // ---------------------------------------------------------------------------
@@ -579,7 +795,9 @@ const char* emit_name(int mode) {
 
 // Two-pass launch.  Scratch: [0, 256) header {walk counter u32, status u32,
 // total i64, emit counter u32}, then tile sums, tile prefixes, counts, run
-// counts, runs.
+// counts, runs.  The separate form (the default) runs the walk, the tile
+// scan and the emit; the fused form runs both passes in one kernel
+// (walk_emit_kernel), whose look-back states take the tile sums' space.
 int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
                 const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
                 int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
@@ -601,15 +819,35 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   uint8_t* nruns = reinterpret_cast<uint8_t*>(p);
   p += a256((size_t)n);
   uint2* runs = reinterpret_cast<uint2*>(p);
-  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead, s));
-
   const int mode = walk_mode(grid);
   const WalkArgs w{ro, rd, n, grid->view(), lat, counts, nruns, runs, tile_sum, walk_counter,
                    status};
   const size_t stage = stage_layout(lat.K, w.g.L, w.g.R, grid->nodes_total(), mode).bytes;
+  const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
+  const bool vec = ((reinterpret_cast<uintptr_t>(ray_idx) | reinterpret_cast<uintptr_t>(t0) |
+                     reinterpret_cast<uintptr_t>(t1)) & 15) == 0;
+  if (sampler_form() == HDDA_SAMPLER_FUSED) {
+    // the look-back states, cleared with the header
+    HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead + a256(8 * (size_t)T), s));
+    unsigned long long* state = reinterpret_cast<unsigned long long*>(tile_sum);
+    KernelTimer kt(walk_emit_name(mode), s);
+    const int st =
+        mode == kModeDense
+            ? launch_walk_emit_mode<kModeDense>(w, stage, skip, state, emit_counter, offsets,
+                                                ray_idx, t0, t1, capacity, vec, total, s)
+        : mode == kModeVdb
+            ? launch_walk_emit_mode<kModeVdb>(w, stage, skip, state, emit_counter, offsets,
+                                              ray_idx, t0, t1, capacity, vec, total, s)
+            : launch_walk_emit_mode<kModeVdbMap>(w, stage, skip, state, emit_counter, offsets,
+                                                 ray_idx, t0, t1, capacity, vec, total, s);
+    if (st != HDDA_OK) return st;
+    kt.stop();
+    if (dev_status) return HDDA_OK;  // stream-ordered: nothing is read back
+    return finish(hw, scratch, capacity, total_out, s);
+  }
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead, s));
   {
     KernelTimer kt(walk_name(mode), s);
-    const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
     const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, skip, s)
                    : mode == kModeVdb ? launch_walk_mode<kModeVdb>(w, stage, skip, s)
                                       : launch_walk_mode<kModeVdbMap>(w, stage, skip, s);
@@ -626,8 +864,6 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   HDDA_CUDA_TRY(cudaGetLastError());
   {
     KernelTimer kt(emit_name(mode), s);
-    const bool vec = ((reinterpret_cast<uintptr_t>(ray_idx) | reinterpret_cast<uintptr_t>(t0) |
-                       reinterpret_cast<uintptr_t>(t1)) & 15) == 0;
     switch (mode) {
       case kModeDense:
         emit_kernel<kModeDense><<<emit_grid<kModeDense>(T), kEmitWarps * 32, 0, s>>>(

@@ -76,7 +76,9 @@ __device__ __forceinline__ bool load_ray(const float* __restrict__ ro,
     ray.d[c] = __ldg(rd + 3 * r + c);
     ok &= isfinite(ray.o[c]) && isfinite(ray.d[c]);
     ray.neg[c] = ray.d[c] < 0.f;
-    ray.inv[c] = 1.0f / ray.d[c];  // estimates only
+    // estimates only; +inf for a zero component (either sign), so that the
+    // crossing estimate needs no test for it (see cross)
+    ray.inv[c] = ray.d[c] != 0.f ? 1.0f / ray.d[c] : INFINITY;
   }
   return ok;
 }
@@ -251,11 +253,13 @@ template <bool kSm>
 __device__ __forceinline__ int cross(const Ray& r, const LatticeDev& lat, const LatHdr& h, int k,
                                      const float e[3], float xo[3]) {
   const int K = lat.K;
-  // estimate: the ray parameter where it meets the first exit plane
+  // estimate: the ray parameter where it meets the first exit plane.  On an
+  // axis the ray does not move along, inv is +inf and the region holds the
+  // point, so e - o > 0 there (or e = +inf): the term is +inf (or NaN when
+  // e - o = 0, which fminf ignores) and sets no bound.
   float te = INFINITY;
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
-    if (r.d[c] != 0.f) te = fminf(te, (e[c] - r.o[c]) * r.inv[c]);
+  for (int c = 0; c < 3; ++c) te = fminf(te, (e[c] - r.o[c]) * r.inv[c]);
   int ke = max(first_k_at<kSm>(lat, h, te), k + 1);
   int lo, hi;  // invariant: point lo inside (lo >= k); point hi outside, or hi == K
   float xp[3];
@@ -480,121 +484,163 @@ __device__ __forceinline__ void expand_warp(int64_t off, int64_t c, bool overflo
   }
 }
 
-// The same expansion with 16-byte stores: lane i writes the four samples at
-// positions base + 4 i .. base + 4 i + 3 of each 128-position block (base a
-// multiple of 4), so ray_idx, t0 and t1 must be 16-byte aligned.  Here the
-// runs hold {first k, first output position relative to the warp's first
-// sample} (see runs_to_positions; unused slots have position INT_MAX), so a
-// lane finds its first position's owner lane and run by two binary searches
-// and then steps through runs and rays; s_end[o] holds the end position of
-// lane o's samples.  Vectors that are partial (the warp's first and last),
-// that reach past capacity, or that touch a ray with more runs than were
-// kept are written element by element (the latter's samples not at all:
-// that ray walks again).
-constexpr uint32_t kNoPosition = 0x7fffffffu;
+// The expansion of the two-pass samplers' emit (separate or fused with the
+// walk), with 16-byte stores.  A warp first lists its
+// tile's runs, rays in order and each ray's runs in order, as records
+// {first output position relative to the tile's first sample, (first k <<
+// 5) | lane}: one per run, or, for a ray with more runs than were kept, one
+// record with kRecSkip set that covers all of that ray's samples (the ray
+// walks again and writes them itself).  A sentinel record with position
+// kRecEnd follows the last.  Positions are then expanded four per lane per
+// 128-position block: a lane finds the record holding its first position
+// by binary search and steps to the next record whenever a position reaches
+// it (a record covers at least one position, so at most once per
+// position).  A sample's k is its record's first k plus its distance from
+// the record's first position; its t0 is the previous sample's t1 when k
+// follows it.  Positions at or past `lim` (the tile's samples, cut off at
+// the buffer's capacity) are not written.
+constexpr int kRecMax = 32 * kMaxRuns;   // records of one 32-ray tile
+constexpr uint32_t kRecSkip = 1u << 31;
+constexpr uint32_t kRecEnd = 0xffffffffu;
 
-// Lane-local rewrite of a lane's kept runs [k_begin, k_end) into {k_begin,
-// first position relative to wbeg}; slots from `kept` on get kNoPosition.
-__device__ __forceinline__ void runs_to_positions(uint2* runs0, int lane, int kept, int64_t off,
-                                                  int64_t wbeg) {
-  uint32_t q = (uint32_t)(off - wbeg);
-  for (int j = 0; j < kMaxRuns; ++j) {
-    uint2& e = runs0[j * 32 + lane];
-    if (j < kept) {
-      const uint32_t len = e.y - e.x;
-      e.y = q;
-      q += len;
-    } else {
-      e = make_uint2(0u, kNoPosition);
+// Lane-local part of the listing: writes this lane's records from index
+// `first` (the lanes' exclusive scan of their record counts).  `c` is the
+// lane's sample count and `q` its first position relative to the tile.
+// `runs_at(j)` returns run j of the lane's ray from memory written in the
+// same kernel (so the caller reads it through L2, not the read-only path).
+__device__ __forceinline__ void list_runs(uint2* rec, int first, int lane, int nr, int64_t c,
+                                          uint32_t q, const uint2* __restrict__ runs_r,
+                                          int64_t stride) {
+  if (c <= 0) return;
+  if (nr > kMaxRuns) {
+    rec[first] = make_uint2(q, kRecSkip | (uint32_t)lane);
+    return;
+  }
+  for (int j0 = 0; j0 < nr; j0 += 4) {
+    uint2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (j0 + u < nr) v[u] = __ldcg(runs_r + (int64_t)(j0 + u) * stride);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (j0 + u < nr) {
+        rec[first + j0 + u] = make_uint2(q, (v[u].x << 5) | (uint32_t)lane);
+        q += v[u].y - v[u].x;
+      }
     }
   }
 }
 
-__device__ __forceinline__ void expand_warp_v4(int64_t off, int64_t c, bool overflow,
-                                               const uint2* runs0, int32_t rid0,
-                                               const int64_t* s_end, const float* __restrict__ t,
-                                               int64_t capacity, int32_t* __restrict__ ray_idx,
+// One record as the expansion uses it: its sample positions q map to
+// lattice index kq + q (kq = first k - first position) and to ray rid0 +
+// lane; `skip` marks a ray that writes its own samples; `nxt` is the next
+// record's first position.
+struct RecView {
+  int kq;
+  int32_t rid;
+  bool skip;
+  uint32_t nxt;
+};
+
+__device__ __forceinline__ RecView rec_view(const uint2* rec, int u, int32_t rid0) {
+  const uint2 r = rec[u];
+  RecView v;
+  v.kq = (int)((r.y & ~kRecSkip) >> 5) - (int)r.x;
+  v.rid = rid0 + (int)(r.y & 31u);
+  v.skip = (r.y & kRecSkip) != 0u;
+  v.nxt = rec[u + 1].x;
+  return v;
+}
+
+// The four positions q0 .. q0 + 3 of one lane, from record u on.  kAll: all
+// four lie in [0, lim) (no bounds test).  Returns in ok[i] whether position
+// q0 + i is written here.
+template <bool kAll>
+__device__ __forceinline__ void expand_four(const uint2* rec, int& u, RecView& v, int q0, int lim,
+                                            int32_t rid0, const float* __restrict__ t,
+                                            int32_t vr[4], float va[4], float vb[4],
+                                            bool ok[4]) {
+  int kprev = -2;
+  float tprev = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int q = q0 + i;
+    ok[i] = kAll || (q >= 0 && q < lim);
+    vr[i] = 0;
+    va[i] = vb[i] = 0.f;
+    if (!ok[i]) continue;
+    if ((uint32_t)q >= v.nxt) v = rec_view(rec, ++u, rid0);  // a record holds >= 1 position
+    ok[i] = !v.skip;
+    if (!ok[i]) continue;
+    const int k = v.kq + q;
+    vr[i] = v.rid;
+    va[i] = k == kprev + 1 ? tprev : __ldg(t + k);
+    vb[i] = __ldg(t + k + 1);
+    kprev = k;
+    tprev = vb[i];
+  }
+}
+
+// Expands the records rec[0 .. nrec) (sentinel at rec[nrec]) of one tile
+// whose first sample goes to output position wbeg.  vec: ray_idx, t0 and t1
+// are 16-byte aligned, so whole 4-position groups take one 16-byte store
+// per array.  Each 128-position block starts from `ufirst`, a record at or
+// before all of its positions (the record of the previous block's last
+// position): lane j reads the first position of record ufirst + j, and a
+// five-step shuffle search gives each lane the last of those 32 records
+// starting at or before its first position; a lane whose position lies
+// beyond them (a block of more than 32 records) binary-searches the rest.
+__device__ __forceinline__ void expand_records(const uint2* rec, int nrec, int lim, int64_t wbeg,
+                                               int32_t rid0, const float* __restrict__ t,
+                                               bool vec, int32_t* __restrict__ ray_idx,
                                                float* __restrict__ t0, float* __restrict__ t1) {
+  if (nrec <= 0 || lim <= 0) return;
   const int lane = threadIdx.x & 31;
-  const int64_t wbeg = __shfl_sync(kFull, off, 0);
-  const int64_t wend = __shfl_sync(kFull, off + c, 31);
-  const unsigned ovf = __ballot_sync(kFull, overflow);
-  // positions relative to the warp's first sample fit in 32 bits (32 rays of
-  // at most 2^24 samples): one shuffle per step of the owner search
-  const int rel = (int)(off - wbeg);
-  for (int64_t base = wbeg & ~(int64_t)3; base < wend; base += 128) {
-    const int64_t q0 = base + 4 * lane;
-    const int64_t qs = max(q0, wbeg);  // first position this warp owns
-    const int qsr = (int)(qs - wbeg);
-    int own = 0;  // the last lane whose offset is <= qs
+  int ufirst = 0;  // rec[0] starts at position 0
+  for (int base = -(int)(wbeg & 3); base < lim; base += 128) {
+    const int q0 = base + 4 * lane;
+    const int qs = max(q0, 0);
+    const uint32_t pj = rec[min(ufirst + lane, nrec)].x;  // the sentinel past the end
+    int j = 0;
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {
-      const int v = __shfl_sync(kFull, rel, own + s);
-      if (v <= qsr) own += s;
+      const uint32_t pv = __shfl_sync(kFull, pj, j + s);
+      if (pv <= (uint32_t)qs) j += s;
     }
-    if (qs >= wend || qs >= q0 + 4) continue;
-    // the run of `own` that holds qs, its first k and the next run's start
-    int j = 0;
-    int k = 0;
-    uint32_t nxt = kNoPosition;
-    if (!((ovf >> own) & 1u)) {
-#pragma unroll
-      for (int s = kMaxRuns / 2; s > 0; s >>= 1)
-        if (runs0[(j + s) * 32 + own].y <= (uint32_t)qsr) j += s;
-      const uint2 e = runs0[j * 32 + own];
-      k = (int)e.x + (qsr - (int)e.y);
-      nxt = j + 1 < kMaxRuns ? runs0[(j + 1) * 32 + own].y : kNoPosition;
+    int u = ufirst + j;
+    if (j == 31 && u < nrec) {  // the record may lie further on: binary search
+      int hi = nrec;  // rec[u] <= qs < rec[hi] (the sentinel)
+      while (hi - u > 1) {
+        const int mid = (u + hi) >> 1;
+        if (rec[mid].x <= (uint32_t)qs) u = mid;
+        else hi = mid;
+      }
     }
     int32_t vr[4];
     float va[4], vb[4];
-    bool ok[4];
-    int o = own;
-    int kprev = -2;      // lattice index of the previous element, and its t_{k+1}
-    float tprev = 0.f;
+    bool ok[4] = {false, false, false, false};
+    if (qs < lim) {
+      RecView v = rec_view(rec, u, rid0);
+      if (base >= 0 && base + 128 <= lim)  // uniform: the whole block is written
+        expand_four<true>(rec, u, v, q0, lim, rid0, t, vr, va, vb, ok);
+      else
+        expand_four<false>(rec, u, v, q0, lim, rid0, t, vr, va, vb, ok);
+      const int64_t p0 = wbeg + q0;
+      if (vec && (ok[0] & ok[1] & ok[2] & ok[3])) {
+        *reinterpret_cast<int4*>(ray_idx + p0) = make_int4(vr[0], vr[1], vr[2], vr[3]);
+        *reinterpret_cast<float4*>(t0 + p0) = make_float4(va[0], va[1], va[2], va[3]);
+        *reinterpret_cast<float4*>(t1 + p0) = make_float4(vb[0], vb[1], vb[2], vb[3]);
+      } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t q = q0 + i;
-      const uint32_t qr = (uint32_t)(q - wbeg);
-      ok[i] = false;
-      vr[i] = 0;
-      va[i] = vb[i] = 0.f;
-      if (q < qs || q >= wend) continue;
-      if (q >= s_end[o]) {  // next ray with samples
-        do {
-          ++o;
-        } while (q >= s_end[o]);
-        j = 0;
-        if (!((ovf >> o) & 1u)) {
-          k = (int)runs0[o].x;
-          nxt = runs0[32 + o].y;
+        for (int i = 0; i < 4; ++i) {
+          if (!ok[i]) continue;
+          ray_idx[p0 + i] = vr[i];
+          t0[p0 + i] = va[i];
+          t1[p0 + i] = vb[i];
         }
-      } else if (qr == nxt) {  // next run of the same ray
-        ++j;
-        k = (int)runs0[j * 32 + o].x;
-        nxt = j + 1 < kMaxRuns ? runs0[(j + 1) * 32 + o].y : kNoPosition;
-      }
-      if ((ovf >> o) & 1u) continue;
-      vr[i] = rid0 + o;
-      va[i] = k == kprev + 1 ? tprev : __ldg(t + k);
-      vb[i] = __ldg(t + k + 1);
-      kprev = k;
-      tprev = vb[i];
-      ok[i] = q < capacity;
-      ++k;
-    }
-    if (ok[0] & ok[1] & ok[2] & ok[3]) {
-      *reinterpret_cast<int4*>(ray_idx + q0) = make_int4(vr[0], vr[1], vr[2], vr[3]);
-      *reinterpret_cast<float4*>(t0 + q0) = make_float4(va[0], va[1], va[2], va[3]);
-      *reinterpret_cast<float4*>(t1 + q0) = make_float4(vb[0], vb[1], vb[2], vb[3]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (!ok[i]) continue;
-        ray_idx[q0 + i] = vr[i];
-        t0[q0 + i] = va[i];
-        t1[q0 + i] = vb[i];
       }
     }
+    ufirst = __shfl_sync(kFull, u, 31);  // the record of this block's last position
   }
 }
 
@@ -636,9 +682,44 @@ __device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, in
   for (int64_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
+// Copies the walk's tables into shared memory at `smem` (stage_layout) and
+// points tb and ls at the copies; the caller synchronises the block before
+// the first walk.
+template <int kMode>
+__device__ __forceinline__ void stage_walk_tables(unsigned char* smem, const GridDev& g,
+                                                  const LatticeDev& lat, const LatHdr& h,
+                                                  Tabs& tb, LatticeDev& ls) {
+  const int64_t nodes = (int64_t)g.L * g.N * g.N * g.N;
+  const StageLayout sl = stage_layout(lat.K, g.L, g.R, nodes, kMode);
+  float* s_tm = reinterpret_cast<float*>(smem + sl.tm);
+  int* s_kidx = reinterpret_cast<int*>(smem + sl.kidx);
+  float* s_thr = reinterpret_cast<float*>(smem + sl.thr);
+  stage_copy(s_tm, lat.tm, lat.K);
+  stage_copy(s_kidx, lat.kidx, (int64_t)h.NB + 2);
+  stage_copy(s_thr, g.thr, (int64_t)g.L * 3 * (g.R + 1));
+  ls.tm = s_tm;
+  ls.kidx = s_kidx;
+  tb.thr = s_thr;
+  if constexpr (kMode == kModeVdb) {
+    uint32_t* s_child = reinterpret_cast<uint32_t*>(smem + sl.child);
+    uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + sl.tile);
+    uint32_t* s_prefix = reinterpret_cast<uint32_t*>(smem + sl.prefix);
+    uint32_t* s_nstate = reinterpret_cast<uint32_t*>(smem + sl.nstate);
+    stage_copy(s_child, g.child, nodes * kNodeWords);
+    stage_copy(s_tile, g.tile, nodes * kNodeWords);
+    stage_copy(s_prefix, g.prefix, nodes * kNodeWords);
+    stage_copy(s_nstate, g.nstate, nodes);
+    tb.child = s_child;
+    tb.tile = s_tile;
+    tb.prefix = s_prefix;
+    tb.nstate = s_nstate;
+  }
+}
+
 // Pass 1.  Persistent: each warp takes 32-ray tiles in order until none is
 // left, so a warp never waits for another.  Writes counts[r], nruns[r]
-// (saturated at 255) and the first kMaxRuns runs at runs[r + j * n].
+// (saturated at 255), the first kMaxRuns runs at runs[r + j * n] and each
+// tile's sample total at tile_sum[tile].
 template <int kMode, bool kSm, bool kSkip, bool kCheck>
 __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
@@ -650,31 +731,7 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
   Tabs tb = global_tabs(g);
   LatticeDev ls = lat;
   if constexpr (kSm) {
-    const int64_t nodes = (int64_t)g.L * g.N * g.N * g.N;
-    const StageLayout sl = stage_layout(lat.K, g.L, g.R, nodes, kMode);
-    float* s_tm = reinterpret_cast<float*>(smem + sl.tm);
-    int* s_kidx = reinterpret_cast<int*>(smem + sl.kidx);
-    float* s_thr = reinterpret_cast<float*>(smem + sl.thr);
-    stage_copy(s_tm, lat.tm, lat.K);
-    stage_copy(s_kidx, lat.kidx, (int64_t)h.NB + 2);
-    stage_copy(s_thr, g.thr, (int64_t)g.L * 3 * (g.R + 1));
-    ls.tm = s_tm;
-    ls.kidx = s_kidx;
-    tb.thr = s_thr;
-    if constexpr (kMode == kModeVdb) {
-      uint32_t* s_child = reinterpret_cast<uint32_t*>(smem + sl.child);
-      uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + sl.tile);
-      uint32_t* s_prefix = reinterpret_cast<uint32_t*>(smem + sl.prefix);
-      uint32_t* s_nstate = reinterpret_cast<uint32_t*>(smem + sl.nstate);
-      stage_copy(s_child, g.child, nodes * kNodeWords);
-      stage_copy(s_tile, g.tile, nodes * kNodeWords);
-      stage_copy(s_prefix, g.prefix, nodes * kNodeWords);
-      stage_copy(s_nstate, g.nstate, nodes);
-      tb.child = s_child;
-      tb.tile = s_tile;
-      tb.prefix = s_prefix;
-      tb.nstate = s_nstate;
-    }
+    stage_walk_tables<kMode>(smem, g, lat, h, tb, ls);
     __syncthreads();
   }
   const int lane = threadIdx.x & 31;

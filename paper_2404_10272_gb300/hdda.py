@@ -21,6 +21,7 @@ OK = 0
 ERR_INVALID_ARG, ERR_CUDA, ERR_CAPACITY, ERR_STEP_LIMIT, ERR_TIMEOUT, ERR_OOM, ERR_INTERNAL = range(1, 8)
 GRID_DENSE, GRID_VDB = 0, 1
 WALK_BRANCH, WALK_SKIP = 0, 1
+SAMPLER_SEPARATE, SAMPLER_FUSED = 0, 1
 (ARRAY_THRESHOLDS, ARRAY_DENSE_BITS, ARRAY_CHILD_MASK, ARRAY_TILE_MASK, ARRAY_LEAF_PREFIX,
  ARRAY_LEAVES, ARRAY_NODE_SUPER, ARRAY_LEAF_SUB, ARRAY_REGION_MAP) = range(9)
 
@@ -31,7 +32,8 @@ EXPORTED = [
     "hdda_traverse_hdda_noalloc", "hdda_grid_set_refine", "hdda_batch_create",
     "hdda_batch_launch", "hdda_batch_results", "hdda_batch_free", "hdda_grid_set_walk",
     "hdda_render", "hdda_grid_update", "hdda_traverse_async", "hdda_set_region_checks",
-    "hdda_region_checks", "hdda_traverse_composite",
+    "hdda_region_checks", "hdda_traverse_composite", "hdda_set_sampler_form",
+    "hdda_sampler_form",
 ]
 
 
@@ -455,6 +457,18 @@ def set_region_checks(on: bool = True):
 def region_checks() -> bool:
     """The current region-check setting."""
     return bool(load().hdda_region_checks())
+
+
+def set_sampler_form(form: int):
+    """Form of the two-pass samplers (process-wide): SAMPLER_SEPARATE
+    (default: the walk and the emit as two kernels) or SAMPLER_FUSED (both
+    passes in one persistent kernel).  Both give the same samples."""
+    _check(load().hdda_set_sampler_form(int(form)))
+
+
+def sampler_form() -> int:
+    """The current sampler form."""
+    return int(load().hdda_sampler_form())
 
 
 def profiler_read() -> dict:

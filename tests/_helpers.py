@@ -1,4 +1,6 @@
 """Shared helpers for the GPU parity tests (not collected by pytest)."""
+import contextlib
+
 import numpy as np
 
 import oracle
@@ -14,6 +16,18 @@ def gpu_samples(hdda, kind, o, d, grid, params, out=None):
     s = fn(o, d, grid, params, out=out)
     off, idx, t0, t1 = s.trimmed()
     return to_np(off), to_np(idx), to_np(t0), to_np(t1)
+
+
+@contextlib.contextmanager
+def sampler_form(hdda, form):
+    """Runs the block with the two-pass samplers in `form` (SAMPLER_SEPARATE or
+    SAMPLER_FUSED), then restores the previous form."""
+    before = hdda.sampler_form()
+    hdda.set_sampler_form(form)
+    try:
+        yield
+    finally:
+        hdda.set_sampler_form(before)
 
 
 def oracle_samples(o, d, occ, aabbs, p):

@@ -50,8 +50,8 @@ def region_map(occ: np.ndarray) -> np.ndarray:
     """Region map of an occupancy grid uint8 [L, R, R, R], in the library's layout:
     uint16 [L, C, C, C] with C = ceil(R / 2).  For each 2^3 cell, the high byte is log2 of
     the edge of the first uniform region in the order 128^3 node (empty or full), 32^3
-    group (empty), 16^3 group (empty), 8^3 block (empty or full), 4^3 cell (empty), 2^3
-    cell (empty or full) -- aligned cubes of the grid padded with empty voxels -- and 0
+    group (empty), 16^3 group (empty), 8^3 block (empty or full), 4^3 cell (empty or
+    full), 2^3 cell (empty or full) -- aligned cubes of the grid padded with empty voxels -- and 0
     when none is; the low byte holds the cell's voxels, bit ((x%2)*2 + y%2)*2 + z%2."""
     L, R = occ.shape[0], occ.shape[1]
     P = -(-R // 128) * 128
@@ -81,7 +81,7 @@ def region_map(occ: np.ndarray) -> np.ndarray:
         done |= m
 
     for s, lg, kinds in ((128, 7, (False, True)), (32, 5, (False,)), (16, 4, (False,)),
-                         (8, 3, (False, True)), (4, 2, (False,)), (2, 1, (False, True))):
+                         (8, 3, (False, True)), (4, 2, (False, True)), (2, 1, (False, True))):
         empty = per_cell(~cubes(s, np.any), s)
         full = per_cell(cubes(s, np.all), s)
         for f in kinds:

@@ -70,6 +70,25 @@ def test_region_check_switch_is_host_only(libpath):
         lib.hdda_set_region_checks(before)
 
 
+def test_sampler_form_switch_is_host_only(libpath):
+    """The sampler-form switch is a host-side setting: separate (0) by default
+    in a fresh process, read back as set, and any other value is refused."""
+    import sys
+    code = ("import ctypes, sys; lib = ctypes.CDLL(sys.argv[1]); "
+            "print(lib.hdda_sampler_form())")
+    out = subprocess.run([sys.executable, "-c", code, libpath], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.strip() == "0", out.stderr
+    lib = ctypes.CDLL(libpath)
+    before = lib.hdda_sampler_form()
+    try:
+        assert lib.hdda_set_sampler_form(1) == 0 and lib.hdda_sampler_form() == 1
+        assert lib.hdda_set_sampler_form(0) == 0 and lib.hdda_sampler_form() == 0
+        assert lib.hdda_set_sampler_form(2) == 1 and lib.hdda_sampler_form() == 0
+        assert lib.hdda_set_sampler_form(-1) == 1 and lib.hdda_sampler_form() == 0
+    finally:
+        lib.hdda_set_sampler_form(before)
+
+
 def test_argument_errors_are_status_codes_before_any_device_call(libpath):
     """Invalid arguments come back as HDDA_ERR_INVALID_ARG with a message,
     checked before the library touches a device (so this runs without one)."""

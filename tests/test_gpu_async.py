@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from paper_2404_10272_gb300 import scenes
-from _helpers import assert_same, to_np
+from _helpers import assert_same, sampler_form, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +66,13 @@ def test_async_equals_sync(H, frame, kind):
     np.testing.assert_array_equal(to_np(cnt.offsets), ref[0])
 
 
-def test_capacity_overflow_clamps_offsets(H, frame):
+@pytest.mark.parametrize("form", ["separate", "fused"])
+def test_capacity_overflow_clamps_offsets(H, frame, form):
+    with sampler_form(H, H.SAMPLER_FUSED if form == "fused" else H.SAMPLER_SEPARATE):
+        _capacity_overflow(H, frame)
+
+
+def _capacity_overflow(H, frame):
     sc, ot, dt, occ, prm = frame
     g = H.build_vdb(occ, sc.aabbs)
     full = H.traverse_hdda(ot, dt, g, prm)

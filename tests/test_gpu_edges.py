@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_2404_10272_gb300 import scenes
-from _helpers import assert_same, gpu_samples, oracle_samples
+from _helpers import assert_same, gpu_samples, oracle_samples, sampler_form
 
 pytestmark = pytest.mark.gpu
 
@@ -30,6 +30,9 @@ def _check(H, occ, aabbs, o, d, p, what):
     assert_same(gpu_samples(H, "hdda", ot, dd, gv, prm), ref, what + " hdda")
     gv.set_refine(False)
     assert_same(gpu_samples(H, "hdda", ot, dd, gv, prm), ref, what + " hdda plain")
+    with sampler_form(H, H.SAMPLER_FUSED):
+        assert_same(gpu_samples(H, "dense", ot, dd, gd, prm), ref, what + " dense fused")
+        assert_same(gpu_samples(H, "hdda", ot, dd, gv, prm), ref, what + " hdda plain fused")
     return ref
 
 
@@ -96,10 +99,17 @@ def test_degenerate_rays(H):
     assert cnt[0] == 0 and cnt[1] == 128 and cnt[5] == 0   # all or nothing for zero directions
 
 
-def test_output_alignment_and_capacity_residues(H):
+@pytest.mark.parametrize("form", ["separate", "fused"])
+def test_output_alignment_and_capacity_residues(H, form):
     """Sample buffers that are not 16-byte aligned take the element-wise
     emit; capacities of every residue mod 4 end the 16-byte stores exactly at
-    capacity on both paths."""
+    capacity on both paths, in both sampler forms."""
+    f = H.SAMPLER_FUSED if form == "fused" else H.SAMPLER_SEPARATE
+    with sampler_form(H, f):
+        _alignment_and_capacity(H)
+
+
+def _alignment_and_capacity(H):
     sc = scenes.tiny_scene()
     o, d = scenes.tiny_camera().rays()
     ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()

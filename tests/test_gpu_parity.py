@@ -11,7 +11,8 @@ import torch
 import oracle
 from paper_2404_10272_gb300 import scenes
 import _layout
-from _helpers import assert_same, gpu_samples, oracle_samples, subset_rays, to_np
+from _helpers import (assert_same, gpu_samples, oracle_samples, sampler_form, slab_scene,
+                      subset_rays, to_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +55,10 @@ def check_all(H, occ, aabbs, o, d, p, what):
         g.set_walk(H.WALK_SKIP)
         assert_same(gpu_samples(H, kind, ot, dt, g, prm), ref, what + f" {kind} skip form")
         g.set_walk(H.WALK_BRANCH)
+    # the walk and the emit fused into one kernel give the same samples
+    with sampler_form(H, H.SAMPLER_FUSED):
+        assert_same(gpu_samples(H, "dense", ot, dt, gd, prm), ref, what + " dense fused")
+        assert_same(gpu_samples(H, "hdda", ot, dt, gv, prm), ref, what + " HDDA fused")
     return ref
 
 
@@ -139,6 +144,30 @@ def test_property_cases(H, levels, res, kind, cone):
     check_all(H, occ, aabbs, o, d, p, f"L{levels} R{res} {kind}")
 
 
+@pytest.mark.parametrize("R,period", [(64, 2), (128, 3)])
+def test_rays_with_many_runs(H, R, period):
+    """Rays crossing more occupied slabs than the walk keeps runs for (16)
+    walk again in the emit and write their own samples; tiles mix them with
+    rays of a few runs (every third ray turned to run along the slabs)."""
+    occ, aabbs, o, d, _, p = slab_scene(R, period, 900, 5000 + R + period)
+    o, d = o.copy(), d.astype(np.float64)
+    # every third ray starts in slab 0 and runs nearly along the slabs: 1 to a few runs
+    o[::3, 0] = 0.5 / R
+    m = o[::3].shape[0]
+    d[::3] = np.stack([np.linspace(0.0, 0.08, m), np.full(m, 0.6), np.full(m, 0.8)], axis=1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    d = d.astype(np.float32)
+    ref = check_all(H, occ, aabbs, o, d, p, f"slabs R{R} period {period}")
+
+    def n_runs(r):
+        a, b = ref[0][r], ref[0][r + 1]
+        return 0 if a == b else 1 + int(np.count_nonzero(ref[2][a + 1:b] != ref[3][a:b - 1]))
+
+    runs = np.array([n_runs(r) for r in range(o.shape[0])])
+    assert (runs[1::3] > 16).mean() > 0.9   # most rays across the slabs overflow the 16 kept runs
+    assert 1 <= runs[::3].min() and runs[::3].max() <= 16
+
+
 def test_tiny_scene_full_frame(H):
     sc = scenes.tiny_scene()
     o, d = scenes.tiny_camera().rays()
@@ -164,6 +193,10 @@ def _full_vs_subset(H, sc, o, d, stride, what):
                     what + " full frame: dense, checks off")
     finally:
         H.set_region_checks(True)
+    with sampler_form(H, H.SAMPLER_FUSED):
+        assert_same(gpu_samples(H, "hdda", ot, dt, gv, prm), vdb, what + " full frame: fused")
+        assert_same(gpu_samples(H, "dense", ot, dt, gd, prm), dense,
+                    what + " full frame: dense, fused")
     # oracle on a stratified subset of the same launch's rays
     so, sd, sel = subset_rays(o, d, stride, offset=stride // 3)
     ref = oracle_samples(so, sd, sc.occ, sc.aabbs, sc.params)
