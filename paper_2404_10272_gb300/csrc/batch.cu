@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kWarps * 32) batch_emit_kernel(
     const uint2* __restrict__ runs, const int64_t* __restrict__ tile_prefix,
     const int64_t* __restrict__ grand_total, int64_t* __restrict__ job_totals,
     unsigned* __restrict__ job_status, unsigned* __restrict__ status) {
-  __shared__ uint2 s_runs[kWarps][kMaxRuns * 32];
+  __shared__ uint2 s_rec[kWarps][kRecMax + 1];
   __shared__ __align__(16) GridDev s_grid[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t t = (int64_t)blockIdx.x * kWarps + warp;
@@ -134,23 +134,19 @@ __global__ void __launch_bounds__(kWarps * 32) batch_emit_kernel(
   const int64_t lr = (t - jt0) * 32 + lane;
   const int64_t gr = t * 32 + lane;
   const int64_t slots = T * 32;
-  const int64_t c = lr < n ? (int64_t)counts[gr] : 0;
+  const int c = lr < n ? counts[gr] : 0;
   const int nr = lr < n ? (int)nruns[gr] : 0;
-  uint2* my_runs = s_runs[warp];
-  if (capacity > 0) {
-    const int kept = min(nr, kMaxRuns);
-    for (int q = 0; __any_sync(kFull, q < kept); ++q)
-      if (q < kept) my_runs[q * 32 + lane] = __ldg(runs + (int64_t)q * slots + gr);
-    __syncwarp();
-  }
-  int64_t inc = c;
+  // a tile holds at most 32 * 2^24 samples: 32-bit positions within it
+  int inc = c;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(kFull, inc, o);
+    const int y = __shfl_up_sync(kFull, inc, o);
     if (lane >= o) inc += y;
   }
+  const int q = inc - c;
   const int64_t base = __ldg(tile_prefix + jt0);
-  const int64_t off = __ldg(tile_prefix + t) - base + inc - c;
+  const int64_t wbeg = __ldg(tile_prefix + t) - base;  // the tile's first sample in the job
+  const int64_t off = wbeg + q;
   if (lr < n) jb.offsets[lr] = off;
   if (t == jt0 + jb.tiles - 1 && lane == 0) {
     const int64_t next = __ldg(tile0 + j + 1);
@@ -160,10 +156,30 @@ __global__ void __launch_bounds__(kWarps * 32) batch_emit_kernel(
     if (capacity > 0 && total > capacity) atomicOr(job_status + j, kJobCapacity);
   }
   if (capacity <= 0) return;
+  // the tile's runs as a record list, expanded with 16-byte stores where the
+  // job's outputs allow (expand_records, walk.cuh)
+  uint2* rec = s_rec[warp];
+  const int kept = c <= 0 ? 0 : nr > kMaxRuns ? 1 : nr;
+  int kinc = kept;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, kinc, o);
+    if (lane >= o) kinc += y;
+  }
+  const int nrec = __shfl_sync(kFull, kinc, 31);
+  list_runs(rec, kinc - kept, lane, nr, c, (uint32_t)q, runs + gr, slots);
+  if (lane == 0) rec[nrec] = make_uint2(kRecEnd, 0u);
+  __syncwarp();
+  const int tot = __shfl_sync(kFull, inc, 31);
+  const int64_t room = capacity - wbeg;
+  const int lim = room <= 0 ? 0 : (int)min((int64_t)tot, room);
+  const bool vec = ((reinterpret_cast<uintptr_t>(jb.ray_idx) |
+                     reinterpret_cast<uintptr_t>(jb.t0) | reinterpret_cast<uintptr_t>(jb.t1)) &
+                    15) == 0;
   const bool overflow = nr > kMaxRuns;
   const LatticeDev lat = jb.lat;
-  expand_warp<true>(off, c, overflow, my_runs, 32, (int32_t)(lr - lane), lat.t, capacity,
-                    jb.ray_idx, jb.t0, jb.t1);
+  expand_records(rec, nrec, lim, wbeg, (int32_t)(lr - lane), lat.t, vec, jb.ray_idx, jb.t0,
+                 jb.t1);
   if (__any_sync(kFull, overflow)) {
     warp_copy_grid(&s_grid[warp], &jb.g);  // the whole warp copies; only overflowing lanes walk
     if (overflow) {

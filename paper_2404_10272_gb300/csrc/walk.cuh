@@ -552,20 +552,18 @@ __device__ __forceinline__ RecView rec_view(const uint2* rec, int u, int32_t rid
   return v;
 }
 
-// The four positions q0 .. q0 + 3 of one lane, from record u on.  kAll: all
-// four lie in [0, lim) (no bounds test).  Returns in ok[i] whether position
+// The four positions q0 .. q0 + 3 of one lane, from record u on, record by
+// record (any number of record changes).  Returns in ok[i] whether position
 // q0 + i is written here.
-template <bool kAll>
-__device__ __forceinline__ void expand_four(const uint2* rec, int& u, RecView& v, int q0, int lim,
-                                            int32_t rid0, const float* __restrict__ t,
-                                            int32_t vr[4], float va[4], float vb[4],
-                                            bool ok[4]) {
-  int kprev = -2;
-  float tprev = 0.f;
+__device__ __forceinline__ void expand_four_any(const uint2* rec, int& u, int q0, int lim,
+                                                int32_t rid0, const float* __restrict__ t,
+                                                int32_t vr[4], float va[4], float vb[4],
+                                                bool ok[4]) {
+  RecView v = rec_view(rec, u, rid0);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int q = q0 + i;
-    ok[i] = kAll || (q >= 0 && q < lim);
+    ok[i] = q >= 0 && q < lim;
     vr[i] = 0;
     va[i] = vb[i] = 0.f;
     if (!ok[i]) continue;
@@ -574,10 +572,8 @@ __device__ __forceinline__ void expand_four(const uint2* rec, int& u, RecView& v
     if (!ok[i]) continue;
     const int k = v.kq + q;
     vr[i] = v.rid;
-    va[i] = k == kprev + 1 ? tprev : __ldg(t + k);
+    va[i] = __ldg(t + k);
     vb[i] = __ldg(t + k + 1);
-    kprev = k;
-    tprev = vb[i];
   }
 }
 
@@ -590,6 +586,9 @@ __device__ __forceinline__ void expand_four(const uint2* rec, int& u, RecView& v
 // five-step shuffle search gives each lane the last of those 32 records
 // starting at or before its first position; a lane whose position lies
 // beyond them (a block of more than 32 records) binary-searches the rest.
+// A lane's four positions then take their lattice index, ray and skip flag
+// from that record or the next one by selects; only a lane whose positions
+// reach a third record steps through them one by one.
 __device__ __forceinline__ void expand_records(const uint2* rec, int nrec, int lim, int64_t wbeg,
                                                int32_t rid0, const float* __restrict__ t,
                                                bool vec, int32_t* __restrict__ ray_idx,
@@ -620,11 +619,25 @@ __device__ __forceinline__ void expand_records(const uint2* rec, int nrec, int l
     float va[4], vb[4];
     bool ok[4] = {false, false, false, false};
     if (qs < lim) {
-      RecView v = rec_view(rec, u, rid0);
-      if (base >= 0 && base + 128 <= lim)  // uniform: the whole block is written
-        expand_four<true>(rec, u, v, q0, lim, rid0, t, vr, va, vb, ok);
-      else
-        expand_four<false>(rec, u, v, q0, lim, rid0, t, vr, va, vb, ok);
+      // The lane's positions lie in record u and, past its end, in record u + 1
+      // (without branches), unless they reach a third record (short runs).
+      const RecView a = rec_view(rec, u, rid0);
+      const RecView b = rec_view(rec, min(u + 1, nrec - 1), rid0);  // used only past a.nxt
+      if ((uint32_t)(q0 + 3) >= b.nxt && a.nxt <= (uint32_t)(q0 + 3)) {
+        expand_four_any(rec, u, q0, lim, rid0, t, vr, va, vb, ok);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int q = q0 + i;
+          const bool in_a = (uint32_t)q < a.nxt;
+          const int k = (in_a ? a.kq : b.kq) + q;
+          vr[i] = in_a ? a.rid : b.rid;
+          ok[i] = q >= 0 && q < lim && !(in_a ? a.skip : b.skip);
+          va[i] = ok[i] ? __ldg(t + k) : 0.f;
+          vb[i] = ok[i] ? __ldg(t + k + 1) : 0.f;
+        }
+        if (a.nxt <= (uint32_t)(q0 + 3)) ++u;  // the record of the lane's last position
+      }
       const int64_t p0 = wbeg + q0;
       if (vec && (ok[0] & ok[1] & ok[2] & ok[3])) {
         *reinterpret_cast<int4*>(ray_idx + p0) = make_int4(vr[0], vr[1], vr[2], vr[3]);
