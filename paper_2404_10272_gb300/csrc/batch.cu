@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kBlock) batch_walk_kernel(
         cur = j;
         warp_copy_grid(&g, &jobs[j].g);
         lat = jobs[j].lat;
-        h = LatHdr{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+        h = lat_hdr(lat);
         n = jobs[j].n;
         job_tile0 = jobs[j].tile0;
         ro = jobs[j].ro;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kWarps * 32) batch_emit_kernel(
     if (overflow) {
       Ray ray;
       load_ray(jb.ro, jb.rd, lr, ray);
-      const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+      const LatHdr h = lat_hdr(lat);
       int unused = 0;
       walk<kMode, true, false>(s_grid[warp], global_tabs(s_grid[warp]), lat, h, ray, nullptr, 0,
                                unused, (int32_t)lr, off, capacity, jb.ray_idx, jb.t0, jb.t1,

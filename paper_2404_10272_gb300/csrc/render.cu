@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kRenderWarps * 32, 6) render_kernel(
   int64_t* gb = s_gbase[wib];
   uint2* sr = s_run[wib];
   unsigned long long evals = 0;  // this warp's blob evaluations
-  const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+  const LatHdr h = lat_hdr(lat);
   const int64_t r = task * kRenderRays + lane;
   const bool has_ray = lane < kRenderRays && r < n;
   bool ok = false;

@@ -45,7 +45,23 @@ LatticeDev lattice_view(char* block, int max_k, int K) {
 struct LatHdr {
   uint32_t key0, shift;
   int NB;
+  int lin;        // constant spacing: tm_k is tm0 + k / inv_dt up to rounding
+  float tm0, inv_dt;
 };
+
+// The lattice header {key0, shift, NB, constant spacing} and, for a lattice
+// of constant spacing, its first midpoint and inverse spacing.
+__device__ __forceinline__ LatHdr lat_hdr(const LatticeDev& lat) {
+  LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2),
+           (int)__ldg(lat.hdr + 3), 0.f, 0.f};
+  if (h.lin && lat.K > 0) {
+    h.tm0 = __ldg(lat.tm);
+    h.inv_dt = 1.0f / (__ldg(lat.t + 1) - __ldg(lat.t));
+  } else {
+    h.lin = 0;
+  }
+  return h;
+}
 
 // First k with tm_k >= te (K if none), through the bucket index.
 template <bool kSm>
@@ -260,7 +276,15 @@ __device__ __forceinline__ int cross(const Ray& r, const LatticeDev& lat, const 
   float te = INFINITY;
 #pragma unroll
   for (int c = 0; c < 3; ++c) te = fminf(te, (e[c] - r.o[c]) * r.inv[c]);
-  int ke = max(first_k_at<kSm>(lat, h, te), k + 1);
+  // With constant spacing, tm_k = tm0 + k dt up to the recurrence's rounding,
+  // so the closed form lands on the first k with tm_k >= te, or next to it,
+  // with fewer instructions than the bucket index.
+  int ke;
+  if (h.lin)  // uniform over the launch
+    ke = (int)ceilf(fminf(fmaxf((te - h.tm0) * h.inv_dt, 0.f), (float)K));
+  else
+    ke = first_k_at<kSm>(lat, h, te);
+  ke = max(ke, k + 1);
   int lo, hi;  // invariant: point lo inside (lo >= k); point hi outside, or hi == K
   float xp[3];
   if (ke >= K) {
@@ -740,7 +764,7 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     uint2* __restrict__ runs, int64_t* __restrict__ tile_sum, unsigned* __restrict__ tile_counter,
     unsigned* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2)};
+  const LatHdr h = lat_hdr(lat);
   Tabs tb = global_tabs(g);
   LatticeDev ls = lat;
   if constexpr (kSm) {
