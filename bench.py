@@ -53,11 +53,11 @@ KERNELS_PER_TIMER = {"build_vdb": 5}   # the builder's timer spans five kernels
 # from the ncu --set full captures (object frame, camera 0; unbounded: its first 200 image
 # rows); dropped like the traffic when a kernel changes.
 PROFILED_COUNTERS = {
-    "object": {"hdda_walk": {"l2_hit_pct": 37.9, "active_lanes_of_32": 24.60},
-               "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 28.98},
+    "object": {"hdda_walk": {"l2_hit_pct": 50.4, "active_lanes_of_32": 24.10},
+               "hdda_emit": {"l2_hit_pct": 10.5, "active_lanes_of_32": 27.37},
                "composite": {"l2_hit_pct": 26.4, "active_lanes_of_32": 30.03}},
-    "unbounded": {"hdda_walk": {"l2_hit_pct": 44.5, "active_lanes_of_32": 24.18},
-                  "hdda_emit": {"l2_hit_pct": 10.3, "active_lanes_of_32": 29.74},
+    "unbounded": {"hdda_walk": {"l2_hit_pct": 48.8, "active_lanes_of_32": 24.20},
+                  "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 30.27},
                   "composite": {"l2_hit_pct": 16.6, "active_lanes_of_32": 30.46}},
 }
 # DRAM bytes (read + write) per launch from ncu of a workload's step on camera 0 (the
@@ -65,8 +65,9 @@ PROFILED_COUNTERS = {
 # entry must be dropped whenever its kernel changes, and a workload without a capture
 # reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 233_595_392, "hdda_emit": 269_224_960, "hdda_walk": 15_702_016},
-    "unbounded": {"composite": 1_502_086_656, "hdda_emit": 2_185_638_400, "hdda_walk": 26_044_672},
+    "object": {"composite": 233_929_216, "hdda_emit": 266_716_160, "hdda_walk": 16_127_232},
+    "unbounded": {"composite": 1_503_472_640, "hdda_emit": 2_183_088_640,
+                  "hdda_walk": 26_714_112},
 }
 
 
@@ -617,9 +618,10 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
 
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
     roofline = roof(dom) if dom else None
-    # the sampler as a whole (walk + emit, or one walk-and-emit kernel): rays in, CSR
-    # offsets and samples out
-    sam_k = ("hdda_walk_emit",) if "hdda_walk_emit" in kern else ("hdda_walk", "hdda_emit")
+    # the sampler as a whole (walk + scan + emit, or one walk-and-emit kernel): rays in,
+    # CSR offsets and samples out
+    sam_k = (("hdda_walk_emit",) if "hdda_walk_emit" in kern
+             else ("hdda_walk", "tile_scan", "hdda_emit"))
     sam_ms = sum(kern[k][1] / max(1, kern[k][0]) for k in sam_k if k in kern)
     roofline_sampler = None
     if sam_ms > 0:

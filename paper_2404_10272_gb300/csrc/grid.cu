@@ -16,7 +16,9 @@
 //   vdb_scatter_kernel  16 threads per partial block copy its mask into the
 //                       compact leaf pool
 //   region_map_kernel   one thread per 2^3-voxel cell: the refined tree's
-//                       region holding the cell, flattened into 16 bits
+//                       region holding the cell, flattened into 16 bits (an
+//                       update that changes no block's state recomputes only
+//                       the changed blocks' cells: region_map_blocks_kernel)
 // The node and scatter kernels also write the refinement masks (occupied
 // 32^3 and 16^3 groups per node, occupied 4^3 and 2^3 cells per leaf) that
 // let hierarchical DDA cross empty space in power-of-two steps below and
@@ -427,10 +429,8 @@ __global__ void vdb_rewrite_leaves_kernel(int B, int N, const int64_t* __restric
 // empty 32^3 and 16^3 groups, empty or tiled 8^3 block, empty or full 4^3
 // cell (full: its eight 2^3 cells are), empty or full 2^3 cell; a cell that
 // is none of these keeps its 8 voxel bits.  Voxels past the grid edge (odd R) are empty in the leaves.
-__global__ void region_map_kernel(GridDev g, uint16_t* __restrict__ rmap) {
+__device__ __forceinline__ uint16_t region_map_cell(const GridDev& g, int64_t idx) {
   const int C = (g.R + 1) >> 1;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)g.L * C * C * C) return;
   int64_t q = idx;
   const int a2 = (int)(q % C);
   q /= C;
@@ -484,7 +484,42 @@ __global__ void region_map_kernel(GridDev g, uint16_t* __restrict__ rmap) {
       mask |= ((lw[v >> 5] >> (v & 31)) & 1u) << u;
     }
   } while (false);
-  rmap[idx] = (uint16_t)((lg << 8) | mask);
+  return (uint16_t)((lg << 8) | mask);
+}
+
+// The whole map, one thread per cell.  With `flags` (an update), only when
+// the update changed the tree's structure.
+__global__ void region_map_kernel(GridDev g, uint16_t* __restrict__ rmap,
+                                  const unsigned* __restrict__ flags) {
+  if (flags && *flags == 0u) return;
+  const int C = (g.R + 1) >> 1;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)g.L * C * C * C) return;
+  rmap[idx] = region_map_cell(g, idx);
+}
+
+// An update that left every block's state as it was (so every node, group
+// and block region stays the same) changes the map only inside the blocks
+// whose voxels changed: their 4^3 cells are recomputed, 64 threads per block.
+__global__ void region_map_blocks_kernel(GridDev g, uint16_t* __restrict__ rmap,
+                                         const int64_t* __restrict__ list, int64_t count,
+                                         const uint8_t* __restrict__ changed,
+                                         const unsigned* __restrict__ flags) {
+  if (*flags != 0u) return;  // the structure changed: the whole map is recomputed
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = t >> 6;
+  if (i >= count || !changed[i]) return;
+  const int64_t blk = list ? list[i] : i;
+  const int B = g.B, C = (g.R + 1) >> 1;
+  const int64_t B3 = (int64_t)B * B * B;
+  const int l = (int)(blk / B3);
+  const int64_t b = blk % B3;
+  const int bx = (int)(b / ((int64_t)B * B)), by = (int)((b / B) % B), bz = (int)(b % B);
+  const int c = (int)(t & 63);
+  const int cx = 4 * bx + (c >> 4), cy = 4 * by + ((c >> 2) & 3), cz = 4 * bz + (c & 3);
+  if (cx >= C || cy >= C || cz >= C) return;  // past the grid edge (R not a multiple of 8)
+  const int64_t idx = (((int64_t)l * C + cx) * C + cy) * C + cz;
+  rmap[idx] = region_map_cell(g, idx);
 }
 
 // ---------------------------------------------------------------------------
@@ -571,7 +606,8 @@ int launch_build(hdda_grid* g, const uint8_t* dense, cudaStream_t s) {
         g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves, g->lsub,
         nullptr);
     HDDA_CUDA_TRY(cudaGetLastError());
-    region_map_kernel<<<blocks_for(g->map_cells(), 256), 256, 0, s>>>(g->view(), g->rmap);
+    region_map_kernel<<<blocks_for(g->map_cells(), 256), 256, 0, s>>>(g->view(), g->rmap,
+                                                                       nullptr);
     kt.stop();
     HDDA_CUDA_TRY(cudaGetLastError());
   }
@@ -684,7 +720,7 @@ int update_vdb(hdda_grid* g, const uint8_t* dense, const int64_t* blocks, int64_
   cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);
   if (e != cudaSuccess) st = cuda_error(e, "cudaMemsetAsync");
   if (st == HDDA_OK) {
-    KernelTimer kt("update_vdb", s);  // the update's six kernels together
+    KernelTimer kt("update_vdb", s);  // the update's seven kernels together
     vdb_update_blocks_kernel<<<blocks_for(count * 32, 256), 256, 0, s>>>(
         dense, g->L, g->R, g->B, blocks, count, g->blk_masks, g->blk_state, changed, flags,
         status);
@@ -699,7 +735,10 @@ int update_vdb(hdda_grid* g, const uint8_t* dense, const int64_t* blocks, int64_
     vdb_rewrite_leaves_kernel<<<blocks_for(count * 16, 256), 256, 0, s>>>(
         g->B, g->N, blocks, count, changed, flags, g->blk_state, g->blk_masks, g->child,
         g->prefix, g->leaves, g->lsub);
-    region_map_kernel<<<blocks_for(g->map_cells(), 256), 256, 0, s>>>(g->view(), g->rmap);
+    region_map_kernel<<<blocks_for(g->map_cells(), 256), 256, 0, s>>>(g->view(), g->rmap,
+                                                                       flags);
+    region_map_blocks_kernel<<<blocks_for(count * 64, 256), 256, 0, s>>>(
+        g->view(), g->rmap, blocks, count, changed, flags);
     kt.stop();
     e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_error(e, "update kernels");
