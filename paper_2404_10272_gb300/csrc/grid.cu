@@ -26,6 +26,7 @@
 // subdivision).  The region map flattens the refined tree for the walk: a
 // ray point's region (its size and occupancy) is one 2-byte load there
 // instead of a descent through node, group, block, leaf and cell masks.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -349,11 +350,15 @@ __global__ void vdb_scatter_kernel(int L, int B, int N, const uint8_t* __restric
                                    uint32_t* __restrict__ leaves, uint32_t* __restrict__ lsub,
                                    const unsigned* __restrict__ gate) {
   if (gate && *gate == 0u) return;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t blk = t >> 4;
-  if (blk >= (int64_t)L * B * B * B) return;
-  if (blk_state[blk] != kBlockPartial) return;
-  scatter_block(blk, (int)(t & 15), B, N, blk_masks, child, prefix, leaves, lsub);
+  // grid-stride, so that an update can launch a small grid that exits at once when
+  // gated off; the stride is a multiple of 16, so a half-warp stays on one block
+  const int64_t total = (int64_t)L * B * B * B * 16;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blk = t >> 4;
+    if (blk_state[blk] != kBlockPartial) continue;
+    scatter_block(blk, (int)(t & 15), B, N, blk_masks, child, prefix, leaves, lsub);
+  }
 }
 
 // Incremental update, step 1: one warp per listed block (every block when
@@ -493,9 +498,10 @@ __global__ void region_map_kernel(GridDev g, uint16_t* __restrict__ rmap,
                                   const unsigned* __restrict__ flags) {
   if (flags && *flags == 0u) return;
   const int C = (g.R + 1) >> 1;
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)g.L * C * C * C) return;
-  rmap[idx] = region_map_cell(g, idx);
+  const int64_t cells = (int64_t)g.L * C * C * C;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < cells;
+       idx += (int64_t)gridDim.x * blockDim.x)  // grid-stride, as vdb_scatter_kernel
+    rmap[idx] = region_map_cell(g, idx);
 }
 
 // An update that left every block's state as it was (so every node, group
@@ -581,6 +587,10 @@ size_t layout(hdda_grid* g, char* base) {
 }
 
 unsigned blocks_for(int64_t threads, int per) { return (unsigned)((threads + per - 1) / per); }
+
+// CTAs of the update's gated grid-stride kernels: eight 256-thread CTAs per SM of a
+// 152-SM GB300, about one resident wave
+constexpr unsigned kGatedCtas = 152 * 8;
 
 int launch_build(hdda_grid* g, const uint8_t* dense, cudaStream_t s) {
   if (g->kind == HDDA_GRID_DENSE) {
@@ -729,14 +739,16 @@ int update_vdb(hdda_grid* g, const uint8_t* dense, const int64_t* blocks, int64_
         g->node_tiles, g->nstate, g->nsuper, flags);
     vdb_finalize_kernel<<<1, 1024, 0, s>>>(g->nodes_total(), g->node_leaves, g->node_tiles,
                                           g->local_prefix, g->prefix, g->totals, flags);
-    vdb_scatter_kernel<<<blocks_for(g->blocks_total() * 16, 256), 256, 0, s>>>(
-        g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix, g->leaves, g->lsub,
-        flags);
+    // the gated kernels run as grid-stride loops over a grid of at most kGatedCtas CTAs,
+    // so that they cost next to nothing when the update changed no block's state
+    vdb_scatter_kernel<<<std::min(blocks_for(g->blocks_total() * 16, 256), kGatedCtas), 256, 0,
+                         s>>>(g->L, g->B, g->N, g->blk_state, g->blk_masks, g->child, g->prefix,
+                              g->leaves, g->lsub, flags);
     vdb_rewrite_leaves_kernel<<<blocks_for(count * 16, 256), 256, 0, s>>>(
         g->B, g->N, blocks, count, changed, flags, g->blk_state, g->blk_masks, g->child,
         g->prefix, g->leaves, g->lsub);
-    region_map_kernel<<<blocks_for(g->map_cells(), 256), 256, 0, s>>>(g->view(), g->rmap,
-                                                                       flags);
+    region_map_kernel<<<std::min(blocks_for(g->map_cells(), 256), kGatedCtas), 256, 0, s>>>(
+        g->view(), g->rmap, flags);
     region_map_blocks_kernel<<<blocks_for(count * 64, 256), 256, 0, s>>>(
         g->view(), g->rmap, blocks, count, changed, flags);
     kt.stop();
