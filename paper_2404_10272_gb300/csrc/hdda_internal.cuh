@@ -87,7 +87,8 @@ constexpr int kKidxMax = 2048;
 // The lattice shared by every ray of a call: t[0..K], tm[0..K-1] (interval
 // midpoints), and a bucket index kidx[0..NB+1] over the order-preserving
 // keys of tm: kidx[b] = first k with key(tm_k) >= key0 + (b << shift).
-// hdr = {key0, shift, NB} lives in device memory next to the tables.
+// hdr = {key0, shift, NB, closed form, ks, A, -, -} lives in device memory
+// next to the tables (the closed form of the index estimate: see lat_hdr).
 struct LatticeDev {
   const float* t;
   const float* tm;
@@ -98,7 +99,7 @@ struct LatticeDev {
 
 // Bytes of one lattice block of capacity max_k: t, tm, kidx and hdr.
 __host__ __device__ constexpr size_t lattice_block_bytes(int max_k) {
-  return (sizeof(float) * (2 * (size_t)max_k + 1) + sizeof(int) * (kKidxMax + 2) + 16 + 255) &
+  return (sizeof(float) * (2 * (size_t)max_k + 1) + sizeof(int) * (kKidxMax + 2) + 32 + 255) &
          ~(size_t)255;
 }
 

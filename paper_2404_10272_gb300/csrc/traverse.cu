@@ -73,7 +73,7 @@ __global__ void lattice_count_kernel(hdda_params p, int64_t* out) {
 }
 
 // Fills t, tm and the bucket index of a lattice block laid out as
-// lattice_block_bytes(max_k): t[max_k+1], tm[max_k], kidx[kKidxMax+2], hdr[4].
+// lattice_block_bytes(max_k): t[max_k+1], tm[max_k], kidx[kKidxMax+2], hdr[8].
 // One CTA: thread 0 runs the recurrence (it is sequential by definition) and
 // sizes the buckets; then every thread fills buckets, each by a binary search
 // for the first k with key(tm_k) >= its lower bound (tm is non-decreasing).
@@ -110,9 +110,27 @@ __global__ void __launch_bounds__(kFillThreads) lattice_fill_kernel(hdda_params 
     hdr[0] = key0;
     hdr[1] = shift;
     hdr[2] = (uint32_t)NB;
-    // constant spacing (no growth with t, or a step the cap always binds):
-    // the walk may estimate indices by the closed form instead of the buckets
-    hdr[3] = (p.cone_angle == 0.f || p.max_step <= p.step) ? 1u : 0u;
+    // A closed form for the walk's index estimates, used instead of the buckets
+    // when it holds: form 1, the spacing is constant; form 2, it is the constant
+    // step up to index ks and then grows geometrically (Delta t = t * cone, so t
+    // and tm gain a factor 1 + cone per index), with the cap max_step never
+    // binding.  A = 1 / log2(1 + cone).
+    uint32_t form = 0;
+    int ks = K;
+    float A = 0.f;
+    if (K > 0) {
+      if (p.cone_angle == 0.f || p.max_step <= p.step) {
+        form = 1;  // constant spacing throughout
+      } else if (__fmul_rn(t_out[K], p.cone_angle) <= p.max_step) {
+        ks = 0;
+        while (ks < K && !(__fmul_rn(t_out[ks], p.cone_angle) > p.step)) ++ks;
+        form = ks < K ? 2 : 1;
+        A = (float)(0.69314718055994531 / log1p((double)p.cone_angle));
+      }
+    }
+    hdr[3] = form;
+    hdr[4] = (uint32_t)ks;
+    hdr[5] = __float_as_uint(A);
   }
   __syncthreads();  // thread 0's table is visible to the block from here on
   if (K == 0) {

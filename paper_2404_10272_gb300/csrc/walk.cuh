@@ -42,21 +42,34 @@ LatticeDev lattice_view(char* block, int max_k, int K) {
   return LatticeDev{t, tm, kidx, hdr, K};
 }
 
+// The lattice header: the bucket index's {key0, shift, NB} and, when the
+// lattice has the closed form (constant spacing up to index ks, geometric
+// growth by 1 + cone per index from there), the values that estimate an
+// index from it: tm_k = tm0 + k dt for k < ks and tm_k = tm_ks (1 + cone)^(k -
+// ks) from ks on, both up to the recurrence's rounding.
 struct LatHdr {
   uint32_t key0, shift;
   int NB;
-  int lin;        // constant spacing: tm_k is tm0 + k / inv_dt up to rounding
+  int lin;        // the closed form: 0 none (buckets), 1 constant spacing, 2 then geometric
   float tm0, inv_dt;
+  float tm_s, inv_tm_s, ks, A;  // tm_ks (+inf when ks = K), 1 / tm_ks, ks, 1 / log2(1 + cone)
 };
 
-// The lattice header {key0, shift, NB, constant spacing} and, for a lattice
-// of constant spacing, its first midpoint and inverse spacing.
 __device__ __forceinline__ LatHdr lat_hdr(const LatticeDev& lat) {
   LatHdr h{__ldg(lat.hdr), __ldg(lat.hdr + 1), (int)__ldg(lat.hdr + 2),
-           (int)__ldg(lat.hdr + 3), 0.f, 0.f};
+           (int)__ldg(lat.hdr + 3), 0.f, 0.f, INFINITY, 0.f, 0.f, 0.f};
   if (h.lin && lat.K > 0) {
+    const int ks = (int)__ldg(lat.hdr + 4);
     h.tm0 = __ldg(lat.tm);
     h.inv_dt = 1.0f / (__ldg(lat.t + 1) - __ldg(lat.t));
+    h.ks = (float)ks;
+    h.A = __uint_as_float(__ldg(lat.hdr + 5));
+    if (h.lin == 2 && ks < lat.K) {
+      h.tm_s = __ldg(lat.tm + ks);
+      h.inv_tm_s = 1.0f / h.tm_s;
+    } else {
+      h.lin = 1;
+    }
   } else {
     h.lin = 0;
   }
@@ -276,14 +289,18 @@ __device__ __forceinline__ int cross(const Ray& r, const LatticeDev& lat, const 
   float te = INFINITY;
 #pragma unroll
   for (int c = 0; c < 3; ++c) te = fminf(te, (e[c] - r.o[c]) * r.inv[c]);
-  // With constant spacing, tm_k = tm0 + k dt up to the recurrence's rounding,
-  // so the closed form lands on the first k with tm_k >= te, or next to it,
-  // with fewer instructions than the bucket index.
+  // The closed form (lat_hdr) lands on the first k with tm_k >= te, or next
+  // to it, with fewer instructions than the bucket index.
   int ke;
-  if (h.lin)  // uniform over the launch
+  if (h.lin == 1) {  // uniform over the launch
     ke = (int)ceilf(fminf(fmaxf((te - h.tm0) * h.inv_dt, 0.f), (float)K));
-  else
+  } else if (h.lin == 2) {
+    const float fc = (te - h.tm0) * h.inv_dt;                  // constant spacing
+    const float fg = fmaf(__log2f(te * h.inv_tm_s), h.A, h.ks);  // geometric growth
+    ke = (int)ceilf(fminf(fmaxf(te < h.tm_s ? fc : fg, 0.f), (float)K));
+  } else {
     ke = first_k_at<kSm>(lat, h, te);
+  }
   ke = max(ke, k + 1);
   int lo, hi;  // invariant: point lo inside (lo >= k); point hi outside, or hi == K
   float xp[3];
