@@ -26,6 +26,7 @@ binary64 compositor) on bounded samples of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -53,10 +54,10 @@ KERNELS_PER_TIMER = {"build_vdb": 5}   # the builder's timer spans five kernels
 # from the ncu --set full captures (object frame, camera 0; unbounded: its first 200 image
 # rows); dropped like the traffic when a kernel changes.
 PROFILED_COUNTERS = {
-    "object": {"hdda_walk": {"l2_hit_pct": 50.4, "active_lanes_of_32": 24.10},
+    "object": {"hdda_walk": {"l2_hit_pct": 50.1, "active_lanes_of_32": 24.16},
                "hdda_emit": {"l2_hit_pct": 10.5, "active_lanes_of_32": 27.37},
                "composite": {"l2_hit_pct": 26.4, "active_lanes_of_32": 30.03}},
-    "unbounded": {"hdda_walk": {"l2_hit_pct": 48.8, "active_lanes_of_32": 24.20},
+    "unbounded": {"hdda_walk": {"l2_hit_pct": 49.0, "active_lanes_of_32": 24.62},
                   "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 30.27},
                   "composite": {"l2_hit_pct": 16.6, "active_lanes_of_32": 30.46}},
 }
@@ -65,9 +66,9 @@ PROFILED_COUNTERS = {
 # entry must be dropped whenever its kernel changes, and a workload without a capture
 # reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 233_929_216, "hdda_emit": 266_716_160, "hdda_walk": 16_127_232},
-    "unbounded": {"composite": 1_503_472_640, "hdda_emit": 2_183_088_640,
-                  "hdda_walk": 26_714_112},
+    "object": {"composite": 233_545_472, "hdda_emit": 266_717_952, "hdda_walk": 16_122_880},
+    "unbounded": {"composite": 1_502_097_152, "hdda_emit": 2_182_912_000,
+                  "hdda_walk": 26_767_616},
 }
 
 
@@ -1055,7 +1056,17 @@ def run_serve(args, quick: bool = False) -> dict:
     lat_ms = []  # latencies of the measured requests of the current mode's repeats
 
     def at_load(ex, lam):
-        """One repeat: the same Poisson arrival sequence (seed 1006) and request mix (seed 7)."""
+        """One repeat: the same Poisson arrival sequence (seed 1006) and request mix (seed 7).
+        Python's cyclic garbage collector is paused during the repeat (as a latency-bound
+        server would run it) and run in between."""
+        gc.collect()
+        gc.disable()
+        try:
+            return _at_load(ex, lam)
+        finally:
+            gc.enable()
+
+    def _at_load(ex, lam):
         pick.seed(7)
         n_req = max(60, int(lam * seconds))
         gaps = np.random.default_rng(1006).exponential(1.0 / lam, size=n_req)
