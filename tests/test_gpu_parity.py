@@ -144,6 +144,33 @@ def test_property_cases(H, levels, res, kind, cone):
     check_all(H, occ, aabbs, o, d, p, f"L{levels} R{res} {kind}")
 
 
+# Lattices of every shape the walk's first guess of a crossing index treats differently:
+# constant spacing (no growth, or a cap below the step), a constant start then geometric
+# growth (from inside the lattice, from its first index, or never reached), and a growth the
+# cap max_step ends (the bucket index).  (near, far, step, cone, max_step)
+LATTICES = [
+    (0.0, 7.0, 0.0123, 0.0, 1e10),    # constant step
+    (0.0, 7.0, 0.01, 0.02, 0.005),    # cap below the step: constant max_step
+    (0.0, 7.0, 0.0123, 0.05, 1e10),   # constant, then geometric from t = 0.246
+    (1.0, 7.0, 0.01, 0.05, 1e10),     # geometric from the first index
+    (0.0, 7.0, 0.05, 0.002, 1e10),    # growth never reached
+    (0.0, 20.0, 0.01, 0.05, 0.2),     # geometric, then capped from t = 4
+]
+
+
+@pytest.mark.parametrize("lattice", LATTICES, ids=[f"lattice{i}" for i in range(len(LATTICES))])
+def test_lattice_shapes(H, lattice):
+    """The samplers stay bit-exact whichever way the crossing search guesses its indices."""
+    near, far, step, cone, max_step = lattice
+    rng = np.random.default_rng(4242)
+    occ = _structured_grid(rng, 2, 24)
+    aabbs = scenes.cascade_boxes(2, 0.8)
+    o, d = _random_rays(rng, 800, 2.5)
+    p = scenes.SamplerParams(near=near, far=far, step=step, cone=cone, max_step=max_step)
+    ref = check_all(H, occ, aabbs, o, d, p, f"lattice {lattice}")
+    assert ref[0][-1] > 0
+
+
 @pytest.mark.parametrize("R,period", [(64, 2), (128, 3)])
 def test_rays_with_many_runs(H, R, period):
     """Rays crossing more occupied slabs than the walk keeps runs for (16)
