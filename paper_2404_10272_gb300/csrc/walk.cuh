@@ -1,11 +1,12 @@
 // walk.cuh -- the per-ray walk shared by the single-call samplers
 // (traverse.cu), the render-only path (render.cu) and the batched sampler
-// (batch.cu): the lattice view and its bucket index, ray loading, exact
-// point evaluation, region location on a dense or VDB grid, the region
-// crossing search, the walk itself (from the start, or resumed after its
-// first runs), the warp-cooperative expansion of runs into samples (4-byte
-// and 16-byte stores), the persistent walk kernel with its staged tables and
-// its launch, and the scan of per-tile sample counts.  How the walk works
+// (batch.cu): the lattice view, its header (closed form and bucket index),
+// ray loading, exact point evaluation, region location on a dense or VDB
+// grid, the region crossing search, the walk itself (from the start, or
+// resumed after its first runs), the warp-cooperative expansion of runs into
+// samples (4-byte stores for the one-pass kernel; a per-tile record list and
+// 16-byte stores for the emits), the persistent walk kernel with its staged
+// tables and its launch, and the scan of per-tile sample counts.  How the walk works
 // and why it is exact is explained at the top of traverse.cu.
 #pragma once
 
@@ -525,30 +526,29 @@ __device__ __forceinline__ void expand_warp(int64_t off, int64_t c, bool overflo
   }
 }
 
-// The expansion of the two-pass samplers' emit (separate or fused with the
-// walk), with 16-byte stores.  A warp first lists its
-// tile's runs, rays in order and each ray's runs in order, as records
-// {first output position relative to the tile's first sample, (first k <<
-// 5) | lane}: one per run, or, for a ray with more runs than were kept, one
-// record with kRecSkip set that covers all of that ray's samples (the ray
-// walks again and writes them itself).  A sentinel record with position
-// kRecEnd follows the last.  Positions are then expanded four per lane per
-// 128-position block: a lane finds the record holding its first position
-// by binary search and steps to the next record whenever a position reaches
-// it (a record covers at least one position, so at most once per
-// position).  A sample's k is its record's first k plus its distance from
-// the record's first position; its t0 is the previous sample's t1 when k
-// follows it.  Positions at or past `lim` (the tile's samples, cut off at
-// the buffer's capacity) are not written.
+// The expansion of the two-pass samplers' emit (separate, fused with the
+// walk, or batched), with 16-byte stores.  A warp first lists its tile's
+// runs, rays in order and each ray's runs in order, as records {first output
+// position relative to the tile's first sample, (first k << 5) | lane}: one
+// per run, or, for a ray with more runs than were kept, one record with
+// kRecSkip set that covers all of that ray's samples (the ray walks again and
+// writes them itself).  A sentinel record with position kRecEnd follows the
+// last.  Positions are then expanded four per lane per 128-position block
+// (expand_records): a lane finds the record holding its first position, and
+// a record covers at least one position, so its four positions lie in at most
+// four consecutive records.  A sample's k is its record's first k plus its
+// distance from the record's first position.  Positions at or past `lim` (the
+// tile's samples, cut off at the buffer's capacity) are not written.
 constexpr int kRecMax = 32 * kMaxRuns;   // records of one 32-ray tile
 constexpr uint32_t kRecSkip = 1u << 31;
 constexpr uint32_t kRecEnd = 0xffffffffu;
 
 // Lane-local part of the listing: writes this lane's records from index
 // `first` (the lanes' exclusive scan of their record counts).  `c` is the
-// lane's sample count and `q` its first position relative to the tile.
-// `runs_at(j)` returns run j of the lane's ray from memory written in the
-// same kernel (so the caller reads it through L2, not the read-only path).
+// lane's sample count and `q` its first position relative to the tile; run j
+// of the lane's ray is runs_r[j * stride].  The runs are read through L2
+// (ld.global.cg), not the read-only path, because the fused sampler form
+// reads them in the kernel that wrote them.
 __device__ __forceinline__ void list_runs(uint2* rec, int first, int lane, int nr, int64_t c,
                                           uint32_t q, const uint2* __restrict__ runs_r,
                                           int64_t stride) {
