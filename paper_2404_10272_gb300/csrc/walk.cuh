@@ -163,14 +163,17 @@ __device__ __forceinline__ void clip_cells(float e[3], const Ray& r, const float
 // those levels need no test, and no half-space, again.  Only finer levels
 // are recorded (the coarsest is tested once per call anyway; measured
 // faster for single-level grids).
-template <int kMode, bool kSm>
-__device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const Ray& r,
-                                       const float x[3], float e[3], unsigned& gone) {
+// kOne: the grid has one level, so the level index is the constant 0 and
+// the level's box, scale and tables are addressed without it.
+template <int kMode, bool kSm, bool kOne>
+__device__ __forceinline__ bool locate_impl(const GridDev& g, const Tabs& tb, const Ray& r,
+                                            const float x[3], float e[3], unsigned& gone) {
+  const int L = kOne ? 1 : g.L;
 #pragma unroll
   for (int c = 0; c < 3; ++c) e[c] = r.neg[c] ? -INFINITY : INFINITY;
   int l = -1;
-  for (int lv = 0; lv < g.L; ++lv) {
-    if (lv + 1 < g.L && ((gone >> lv) & 1u)) continue;
+  for (int lv = 0; lv < L; ++lv) {
+    if (lv + 1 < L && ((gone >> lv) & 1u)) continue;
     const LevelDev& B = g.lv[lv];
     bool inside = true;
 #pragma unroll
@@ -198,7 +201,7 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
       }
     }
     if (never) {
-      if (lv + 1 < g.L) gone |= 1u << lv;
+      if (lv + 1 < L) gone |= 1u << lv;
       continue;
     }
     if (best < 0) continue;
@@ -210,8 +213,9 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
     }
   }
   if (l < 0) return false;
+  if constexpr (kOne) l = 0;
 
-  const LevelDev& V = g.lv[l];
+  const LevelDev& V = g.lv[kOne ? 0 : l];
   int i[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -275,6 +279,13 @@ __device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const R
     clip_cells<kSm>(e, r, thr, R1, c, a0, min(a0 + sz, g.R));
   }
   return occ;
+}
+
+template <int kMode, bool kSm>
+__device__ __forceinline__ bool locate(const GridDev& g, const Tabs& tb, const Ray& r,
+                                       const float x[3], float e[3], unsigned& gone) {
+  if (g.L == 1) return locate_impl<kMode, kSm, true>(g, tb, r, x, e, gone);  // uniform
+  return locate_impl<kMode, kSm, false>(g, tb, r, x, e, gone);
 }
 
 // First k' in (k, K] whose point is outside the region (K if none).  The
@@ -459,7 +470,9 @@ __device__ __forceinline__ int walk_from(const GridDev& g, const Tabs& tb, const
   unsigned gone = 0u;
   while (k < K) {
     float e[3];
-    const bool occ = locate<kMode, kSm>(g, tb, r, x, e, gone);
+    // the general form only: this path is rare, and one copy of the location
+    // code keeps its caller's registers free
+    const bool occ = locate_impl<kMode, kSm, false>(g, tb, r, x, e, gone);
     const int kn = cross<kSm>(r, lat, h, k, e, x);
     if (occ) {
       if (k == re) {
