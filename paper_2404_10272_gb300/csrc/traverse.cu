@@ -348,36 +348,26 @@ __global__ void __launch_bounds__(kBS) onepass_kernel(
 constexpr int kEmitWarps = 4;
 
 // Pass 2 for one 32-ray tile, independent of every other tile: its offset
-// is the tile's prefix plus a warp scan; its runs become a record list in
-// shared memory (rec: kRecMax records and a sentinel) that expand_records
-// turns into samples.  A ray with more runs than were kept walks again.
-// The per-ray words of a tile that pass 2 starts from: the lane's sample
-// count and run count, and the tile's first output position.
-struct TileHead {
-  int c, nr;
-  int64_t wbeg;
-};
-
-__device__ __forceinline__ TileHead load_tile_head(int64_t tile, int64_t n,
-                                                   const int32_t* __restrict__ counts,
-                                                   const uint8_t* __restrict__ nruns,
-                                                   const int64_t* __restrict__ tile_prefix) {
-  const int64_t r = tile * 32 + (threadIdx.x & 31);
-  return TileHead{r < n ? counts[r] : 0, r < n ? (int)nruns[r] : 0, __ldg(tile_prefix + tile)};
-}
-
+// is the sum of the earlier tiles' samples (tile_offset, from the group sums
+// the walk kept) plus a warp scan; its runs become a record list in shared
+// memory (rec: kRecMax records and a sentinel) that expand_records turns into
+// samples.  A ray with more runs than were kept walks again.  The last tile
+// writes the total.
 template <int kMode>
 __device__ __forceinline__ void emit_tile(
-    int64_t tile, const TileHead& th, uint2* rec, const float* __restrict__ ro,
+    int64_t tile, unsigned T, uint2* rec, const float* __restrict__ ro,
     const float* __restrict__ rd, int64_t n, const GridDev& g, const LatticeDev& lat,
-    const uint2* __restrict__ runs, int64_t* __restrict__ offsets,
+    const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
+    const uint2* __restrict__ runs, const int64_t* __restrict__ tile_sum,
+    const unsigned long long* __restrict__ sums32,
+    const unsigned long long* __restrict__ sums1024, int64_t* __restrict__ offsets,
     int32_t* __restrict__ ray_idx, float* __restrict__ t0, float* __restrict__ t1,
-    int64_t capacity, bool vec, unsigned* __restrict__ status) {
+    int64_t capacity, bool vec, int64_t* __restrict__ total, unsigned* __restrict__ status) {
   const int lane = threadIdx.x & 31;
   const int64_t r = tile * 32 + lane;
-  const int c = th.c;
-  const int nr = th.nr;
-  const int64_t wbeg = th.wbeg;
+  const int c = r < n ? counts[r] : 0;
+  const int nr = r < n ? (int)nruns[r] : 0;
+  const int64_t wbeg = tile_offset(tile, tile_sum, sums32, sums1024);
   // a tile holds at most 32 * 2^24 samples: 32-bit positions within it
   int inc = c;
 #pragma unroll
@@ -388,6 +378,7 @@ __device__ __forceinline__ void emit_tile(
   const int q = inc - c;
   const int tot = __shfl_sync(kFull, inc, 31);
   const int64_t off = wbeg + q;
+  if (tile == (int64_t)T - 1 && lane == 0) *total = wbeg + tot;
   if (capacity > 0) {
     // with too small a buffer the CSR offsets are clamped to it, so that a
     // consumer of the arrays stays in bounds; the status says what happened
@@ -396,6 +387,7 @@ __device__ __forceinline__ void emit_tile(
     if (wbeg + tot > capacity && lane == 0) atomicOr(status, kDevCapacity);
   } else {
     if (r < n) offsets[r] = off;
+    if (r == n - 1) offsets[n] = off + c;
     return;
   }
   const int kept = c <= 0 ? 0 : nr > kMaxRuns ? 1 : nr;
@@ -428,12 +420,14 @@ __device__ __forceinline__ void emit_tile(
 // tile and loading its counts before expanding the current one measured 5-14 %
 // slower: tiles held by busy warps lengthen the tail.)
 template <int kMode>
-__global__ void __launch_bounds__(kEmitWarps * 32, 8) emit_kernel(
+__global__ void __launch_bounds__(kEmitWarps * 32, 7) emit_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, const int32_t* __restrict__ counts, const uint8_t* __restrict__ nruns,
-    const uint2* __restrict__ runs, const int64_t* __restrict__ tile_prefix,
-    int64_t* __restrict__ offsets, int32_t* __restrict__ ray_idx, float* __restrict__ t0,
-    float* __restrict__ t1, int64_t capacity, bool vec, unsigned* __restrict__ tile_counter,
+    const uint2* __restrict__ runs, const int64_t* __restrict__ tile_sum,
+    const unsigned long long* __restrict__ sums32,
+    const unsigned long long* __restrict__ sums1024, int64_t* __restrict__ offsets,
+    int32_t* __restrict__ ray_idx, float* __restrict__ t0, float* __restrict__ t1,
+    int64_t capacity, bool vec, unsigned* __restrict__ tile_counter, int64_t* __restrict__ total,
     unsigned* __restrict__ status) {
   __shared__ uint2 s_rec[kEmitWarps][kRecMax + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -443,9 +437,8 @@ __global__ void __launch_bounds__(kEmitWarps * 32, 8) emit_kernel(
     if (lane == 0) tile = atomicAdd(tile_counter, 1u);
     tile = __shfl_sync(kFull, tile, 0);
     if (tile >= T) break;
-    const TileHead th = load_tile_head(tile, n, counts, nruns, tile_prefix);
-    emit_tile<kMode>(tile, th, s_rec[warp], ro, rd, n, g, lat, runs, offsets, ray_idx, t0, t1,
-                     capacity, vec, status);
+    emit_tile<kMode>(tile, T, s_rec[warp], ro, rd, n, g, lat, counts, nruns, runs, tile_sum,
+                     sums32, sums1024, offsets, ray_idx, t0, t1, capacity, vec, total, status);
     __syncwarp();  // the next tile reuses this warp's shared memory
   }
 }
@@ -836,10 +829,12 @@ const char* emit_name(int mode) {
 }
 
 // Two-pass launch.  Scratch: [0, 256) header {walk counter u32, status u32,
-// total i64, emit counter u32}, then tile sums, tile prefixes, counts, run
-// counts, runs.  The separate form (the default) runs the walk, the tile
-// scan and the emit; the fused form runs both passes in one kernel
-// (walk_emit_kernel), whose look-back states take the tile sums' space.
+// total i64, emit counter u32}, then tile sums, the walk's group sums (per 32
+// and per 1024 tiles), counts, run counts, runs.  The separate form (the
+// default) runs the walk and the emit, which takes each tile's offset from
+// the tile and group sums (no scan kernel in between); the fused form runs
+// both passes in one kernel (walk_emit_kernel), whose look-back states take
+// the tile sums' space.
 int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
                 const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
                 int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
@@ -849,12 +844,17 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   unsigned* status = dev_status ? dev_status : walk_counter + 1;
   int64_t* total = reinterpret_cast<int64_t*>(scratch + 8);
   unsigned* emit_counter = reinterpret_cast<unsigned*>(scratch + 16);
-  // the parallel scan takes up to kMaxSupers * kSuperTiles tiles; larger calls scan in one CTA
-  const bool par_scan = T <= (int64_t)kMaxSupers * kSuperTiles;
+  // region A (after the header): the group sums of the separate form,
+  // ceil(T / 32) per 32 tiles then ceil(T / 1024) per 1024 tiles, or the
+  // look-back states of the fused form; region B: the tile sums.  Both forms
+  // clear the header and what they use of region A with one memset.
   char* p = scratch + kTwopassHead;
-  int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
+  const int64_t G32 = (T + 31) / 32, G1024 = (T + 1023) / 1024;
+  unsigned long long* sums32 = reinterpret_cast<unsigned long long*>(p);
+  unsigned long long* sums1024 = sums32 + G32;
+  unsigned long long* state = sums32;
   p += a256(8 * (size_t)T);
-  int64_t* tile_prefix = reinterpret_cast<int64_t*>(p);
+  int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
   p += a256(8 * (size_t)T);
   int32_t* counts = reinterpret_cast<int32_t*>(p);
   p += a256(4 * (size_t)n);
@@ -862,16 +862,14 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
   p += a256((size_t)n);
   uint2* runs = reinterpret_cast<uint2*>(p);
   const int mode = walk_mode(grid);
-  const WalkArgs w{ro, rd, n, grid->view(), lat, counts, nruns, runs, tile_sum, walk_counter,
-                   status};
+  WalkArgs w{ro, rd, n, grid->view(), lat, counts, nruns, runs, tile_sum, walk_counter,
+             status};
   const size_t stage = stage_layout(lat.K, w.g.L, w.g.R, grid->nodes_total(), mode).bytes;
   const bool skip = grid->walk_variant == HDDA_WALK_SKIP;
   const bool vec = ((reinterpret_cast<uintptr_t>(ray_idx) | reinterpret_cast<uintptr_t>(t0) |
                      reinterpret_cast<uintptr_t>(t1)) & 15) == 0;
   if (sampler_form() == HDDA_SAMPLER_FUSED) {
-    // the look-back states, cleared with the header
-    HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead + a256(8 * (size_t)T), s));
-    unsigned long long* state = reinterpret_cast<unsigned long long*>(tile_sum);
+    HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead + 8 * (size_t)T, s));
     KernelTimer kt(walk_emit_name(mode), s);
     const int st =
         mode == kModeDense
@@ -887,7 +885,9 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
     if (dev_status) return HDDA_OK;  // stream-ordered: nothing is read back
     return finish(hw, scratch, capacity, total_out, s);
   }
-  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead, s));
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead + 8 * (size_t)(G32 + G1024), s));
+  w.sums32 = sums32;
+  w.sums1024 = sums1024;
   {
     KernelTimer kt(walk_name(mode), s);
     const int st = mode == kModeDense ? launch_walk_mode<kModeDense>(w, stage, skip, s)
@@ -896,31 +896,22 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
     if (st != HDDA_OK) return st;
   }
   {
-    KernelTimer kt("tile_scan", s);
-    if (par_scan)
-      tile_scan_par_kernel<<<(unsigned)((T + kSuperTiles - 1) / kSuperTiles), kSuperTiles, 0, s>>>(
-          tile_sum, T, tile_prefix, total, offsets + n);
-    else
-      tile_scan_kernel<<<1, kScanThreads, 0, s>>>(tile_sum, T, tile_prefix, total, offsets + n);
-  }
-  HDDA_CUDA_TRY(cudaGetLastError());
-  {
     KernelTimer kt(emit_name(mode), s);
     switch (mode) {
       case kModeDense:
         emit_kernel<kModeDense><<<emit_grid<kModeDense>(T), kEmitWarps * 32, 0, s>>>(
-            ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, vec, emit_counter, status);
+            ro, rd, n, w.g, lat, counts, nruns, runs, tile_sum, sums32, sums1024, offsets,
+            ray_idx, t0, t1, capacity, vec, emit_counter, total, status);
         break;
       case kModeVdb:
         emit_kernel<kModeVdb><<<emit_grid<kModeVdb>(T), kEmitWarps * 32, 0, s>>>(
-            ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, vec, emit_counter, status);
+            ro, rd, n, w.g, lat, counts, nruns, runs, tile_sum, sums32, sums1024, offsets,
+            ray_idx, t0, t1, capacity, vec, emit_counter, total, status);
         break;
       default:
         emit_kernel<kModeVdbMap><<<emit_grid<kModeVdbMap>(T), kEmitWarps * 32, 0, s>>>(
-            ro, rd, n, w.g, lat, counts, nruns, runs, tile_prefix, offsets, ray_idx, t0, t1,
-            capacity, vec, emit_counter, status);
+            ro, rd, n, w.g, lat, counts, nruns, runs, tile_sum, sums32, sums1024, offsets,
+            ray_idx, t0, t1, capacity, vec, emit_counter, total, status);
         break;
     }
   }

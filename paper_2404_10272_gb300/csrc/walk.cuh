@@ -792,7 +792,8 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, int32_t* __restrict__ counts, uint8_t* __restrict__ nruns_out,
     uint2* __restrict__ runs, int64_t* __restrict__ tile_sum, unsigned* __restrict__ tile_counter,
-    unsigned* __restrict__ status) {
+    unsigned* __restrict__ status, unsigned long long* __restrict__ sums32,
+    unsigned long long* __restrict__ sums1024) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LatHdr h = lat_hdr(lat);
   Tabs tb = global_tabs(g);
@@ -821,8 +822,35 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-    if (lane == 0) tile_sum[tile] = c;
+    if (lane == 0) {
+      tile_sum[tile] = c;
+      if (sums32) {  // the group sums tile_offset reads (zeroed by the caller)
+        atomicAdd(sums32 + (tile >> 5), (unsigned long long)c);
+        atomicAdd(sums1024 + (tile >> 10), (unsigned long long)c);
+      }
+    }
   }
+}
+
+// The first output position of tile t: the sum of every earlier tile's
+// samples, from the sums the walk kept per 1024 tiles and per 32 tiles and
+// the tile sums themselves (at most 31 + 31 entries of the last two, and
+// t / 1024 of the first, read by the warp's lanes at once).  Called by a
+// whole warp; every lane returns the offset.
+__device__ __forceinline__ int64_t tile_offset(int64_t t, const int64_t* __restrict__ tile_sum,
+                                               const unsigned long long* __restrict__ sums32,
+                                               const unsigned long long* __restrict__ sums1024) {
+  const int lane = threadIdx.x & 31;
+  int64_t v = 0;
+  const int64_t g2 = t >> 10;  // whole 1024-tile groups before t
+  for (int64_t j = lane; j < g2; j += 32) v += (int64_t)__ldg(sums1024 + j);
+  const int64_t g1 = (g2 << 5) + lane;  // 32-tile groups of t's 1024-tile group before t's
+  if (g1 < (t >> 5)) v += (int64_t)__ldg(sums32 + g1);
+  const int64_t j0 = ((t >> 5) << 5) + lane;  // tiles of t's 32-tile group before t
+  if (j0 < t) v += __ldg(tile_sum + j0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -847,6 +875,8 @@ struct WalkArgs {
   int64_t* tile_sum;
   unsigned* counter;
   unsigned* status;
+  unsigned long long* sums32 = nullptr;    // optional group sums for tile_offset
+  unsigned long long* sums1024 = nullptr;
 };
 
 template <int kMode, bool kSm, bool kSkip>
@@ -869,7 +899,7 @@ int launch_walk(const WalkArgs& w, size_t smem, cudaStream_t s) {
   const int64_t full = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   const unsigned grid = (unsigned)(want < full ? want : full);
   kern<<<grid, kWalkBS, smem, s>>>(w.ro, w.rd, w.n, w.g, w.lat, w.counts, w.nruns, w.runs,
-                                   w.tile_sum, w.counter, w.status);
+                                   w.tile_sum, w.counter, w.status, w.sums32, w.sums1024);
   HDDA_CUDA_TRY(cudaGetLastError());
   return HDDA_OK;
 }
