@@ -54,11 +54,11 @@ KERNELS_PER_TIMER = {"build_vdb": 5}   # the builder's timer spans five kernels
 # from the ncu --set full captures (object frame, camera 0; unbounded: its first 200 image
 # rows); dropped like the traffic when a kernel changes.
 PROFILED_COUNTERS = {
-    "object": {"hdda_walk": {"l2_hit_pct": 50.1, "active_lanes_of_32": 24.16},
-               "hdda_emit": {"l2_hit_pct": 10.5, "active_lanes_of_32": 27.37},
+    "object": {"hdda_walk": {"l2_hit_pct": 50.7, "active_lanes_of_32": 23.79},
+               "hdda_emit": {"l2_hit_pct": 10.7, "active_lanes_of_32": 27.16},
                "composite": {"l2_hit_pct": 26.4, "active_lanes_of_32": 30.03}},
-    "unbounded": {"hdda_walk": {"l2_hit_pct": 49.0, "active_lanes_of_32": 24.62},
-                  "hdda_emit": {"l2_hit_pct": 10.2, "active_lanes_of_32": 30.27},
+    "unbounded": {"hdda_walk": {"l2_hit_pct": 49.2, "active_lanes_of_32": 24.59},
+                  "hdda_emit": {"l2_hit_pct": 10.0, "active_lanes_of_32": 30.15},
                   "composite": {"l2_hit_pct": 16.6, "active_lanes_of_32": 30.46}},
 }
 # DRAM bytes (read + write) per launch from ncu of a workload's step on camera 0 (the
@@ -66,9 +66,9 @@ PROFILED_COUNTERS = {
 # entry must be dropped whenever its kernel changes, and a workload without a capture
 # reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 233_545_472, "hdda_emit": 266_717_952, "hdda_walk": 16_122_880},
-    "unbounded": {"composite": 1_502_097_152, "hdda_emit": 2_182_912_000,
-                  "hdda_walk": 26_767_616},
+    "object": {"composite": 233_765_120, "hdda_emit": 266_570_240, "hdda_walk": 16_123_648},
+    "unbounded": {"composite": 1_502_329_856, "hdda_emit": 2_182_360_576,
+                  "hdda_walk": 26_761_728},
 }
 
 
@@ -619,10 +619,10 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
 
     dom = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
     roofline = roof(dom) if dom else None
-    # the sampler as a whole (walk + scan + emit, or one walk-and-emit kernel): rays in,
-    # CSR offsets and samples out
+    # the sampler as a whole (walk then emit, or one walk-and-emit kernel): rays in, CSR
+    # offsets and samples out
     sam_k = (("hdda_walk_emit",) if "hdda_walk_emit" in kern
-             else ("hdda_walk", "tile_scan", "hdda_emit"))
+             else ("hdda_walk", "hdda_emit"))
     sam_ms = sum(kern[k][1] / max(1, kern[k][0]) for k in sam_k if k in kern)
     roofline_sampler = None
     if sam_ms > 0:

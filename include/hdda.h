@@ -551,9 +551,10 @@ int hdda_region_checks(void);
 /*
  * Form of the two-pass samplers (hdda_traverse_dense, hdda_traverse_hdda,
  * hdda_traverse_async); the samples are the same in both.
- *   HDDA_SAMPLER_SEPARATE (default): the walk (pass 1), a scan of the
- *     per-tile sample totals (the prefix sum of Algorithm 1's per-ray sample
- *     counts, for the output offsets) and the emit (pass 2) as three kernels.
+ *   HDDA_SAMPLER_SEPARATE (default): the walk (pass 1) and the emit (pass 2)
+ *     as two kernels; the walk also keeps sample totals per 32 and per 1024
+ *     tiles, from which the emit adds up each tile's output offset (the
+ *     prefix sum of Algorithm 1's per-ray sample counts).
  *   HDDA_SAMPLER_FUSED: one persistent kernel; its warps walk 32-ray tiles
  *     until none is left, then write tiles out in order, each tile's offset
  *     from a decoupled look-back over the totals the walks published, so

@@ -33,17 +33,17 @@
 // The result is the sample set of the definition, with dense DDA and HDDA
 // bit-identical; HDDA just crosses far fewer regions.
 //
-// Launch shapes.  The allocating entry points run, by default, three
-// kernels: walk_kernel (persistent warps take 32-ray tiles in order from an
-// atomic counter and walk them with the lattice, bucket, threshold and node
-// tables staged in shared memory; each ray's sample count and merged
-// occupied runs go to global memory, with no CTA barrier anywhere, plus one
-// sum per 32-ray tile), tile_scan_par_kernel (prefix sums of the tile sums),
-// and emit_kernel (persistent warps again, one 32-ray tile at a time: the
-// tile's prefix plus a warp scan gives each ray's offset; it writes the CSR
-// offsets and expands its rays' runs into (ray, t_k, t_k+1) samples through
-// a record list in shared memory, with coalesced 16-byte stores, four
-// samples per lane).  With hdda_set_sampler_form(HDDA_SAMPLER_FUSED) one
+// Launch shapes.  The allocating entry points run, by default, two kernels:
+// walk_kernel (persistent warps take 32-ray tiles in order from an atomic
+// counter and walk them with the lattice, bucket, threshold and node tables
+// staged in shared memory; each ray's sample count and merged occupied runs
+// go to global memory, with no CTA barrier anywhere, plus one sum per 32-ray
+// tile, also added to sums per 32 and per 1024 tiles) and emit_kernel
+// (persistent warps again, one 32-ray tile at a time: the sums of the earlier
+// tiles (tile_offset) plus a warp scan give each ray's offset; it writes the
+// CSR offsets and expands its rays' runs into (ray, t_k, t_k+1) samples
+// through a record list in shared memory, with coalesced 16-byte stores,
+// four samples per lane).  With hdda_set_sampler_form(HDDA_SAMPLER_FUSED) one
 // kernel, walk_emit_kernel, does the walk and the emit, the offsets coming
 // from a decoupled look-back.  The allocation-free entry point runs one
 // kernel, onepass_kernel, whose CTAs keep the runs in shared memory and look
