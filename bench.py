@@ -54,11 +54,9 @@ KERNELS_PER_TIMER = {"build_vdb": 5}   # the builder's timer spans five kernels
 # from the ncu --set full captures (object frame, camera 0; unbounded: its first 200 image
 # rows); dropped like the traffic when a kernel changes.
 PROFILED_COUNTERS = {
-    "object": {"hdda_walk": {"l2_hit_pct": 50.7, "active_lanes_of_32": 23.79},
-               "hdda_emit": {"l2_hit_pct": 10.7, "active_lanes_of_32": 27.16},
+    "object": {"hdda_emit": {"l2_hit_pct": 10.7, "active_lanes_of_32": 27.16},
                "composite": {"l2_hit_pct": 26.4, "active_lanes_of_32": 30.03}},
-    "unbounded": {"hdda_walk": {"l2_hit_pct": 49.2, "active_lanes_of_32": 24.59},
-                  "hdda_emit": {"l2_hit_pct": 10.0, "active_lanes_of_32": 30.15},
+    "unbounded": {"hdda_emit": {"l2_hit_pct": 10.0, "active_lanes_of_32": 30.15},
                   "composite": {"l2_hit_pct": 16.6, "active_lanes_of_32": 30.46}},
 }
 # DRAM bytes (read + write) per launch from ncu of a workload's step on camera 0 (the
@@ -66,9 +64,8 @@ PROFILED_COUNTERS = {
 # entry must be dropped whenever its kernel changes, and a workload without a capture
 # reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 233_765_120, "hdda_emit": 266_570_240, "hdda_walk": 16_123_648},
-    "unbounded": {"composite": 1_502_329_856, "hdda_emit": 2_182_360_576,
-                  "hdda_walk": 26_761_728},
+    "object": {"composite": 233_765_120, "hdda_emit": 266_570_240},
+    "unbounded": {"composite": 1_502_329_856, "hdda_emit": 2_182_360_576},
 }
 
 
@@ -218,7 +215,7 @@ def object_summary(d: dict) -> dict:
     """The object-centric frame's figures for the headline line's `object` key."""
     keep = ("ms_per_step", "value", "samples_per_step", "hdda_sampler", "dense_dda_sampler",
             "hdda_vs_dense_sampler_speedup", "roofline", "roofline_sampler", "render_only_step",
-            "dense_dda_step", "grid", "candidates_per_ray", "fused_sampler_form")
+            "dense_dda_step", "grid", "candidates_per_ray", "fused_sampler_form", "ray_order")
     out = {"workload": d["config"]["workload"], "rays_per_step": d["config"]["rays_per_step"],
            "steps": d["steps"], "rays_per_s": d["value"]}
     out.update({k: d[k] for k in keep if k in d and k != "value"})
@@ -247,7 +244,13 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
     dense = torch.from_numpy(sc.occ).cuda()
     field = torch.from_numpy(sc.field).cuda()
     p = sc.params
-    prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    # the rays are each camera's pixels row by row: the calls pass the image width, so that
+    # the walk takes them in 8 x 4 pixel blocks (same outputs); `ray_order` below times the
+    # walk in index order beside it
+    img_w = cams[0].width
+    prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps,
+                           image_width=img_w)
+    prm_index = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
     gv = hdda.build_vdb(dense, sc.aabbs)
     gd = hdda.pack_dense(dense, sc.aabbs)
     gvp = hdda.build_vdb(dense, sc.aabbs)   # the plain VDB tree, without refinement masks
@@ -390,6 +393,15 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
         ms_fu_s, _, _, _ = timed(sampler_hdda, K, 2)
     finally:
         hdda.set_sampler_form(hdda.SAMPLER_SEPARATE)
+    # the same step and samplers with the rays walked in index order (no image width):
+    # the closures above read `prm` when they run
+    prm_blocks, prm = prm, prm_index
+    try:
+        ms_io, _, kern_io, _ = timed(step_hdda, K, 2, profile=True)
+        ms_io_s, _, _, _ = timed(sampler_hdda, K, 2)
+        ms_io_d, _, _, _ = timed(sampler_dense, K2, 2)
+    finally:
+        prm = prm_blocks
     ms_sync = ms_sp = ms_ss = ms_ds = ms_f = None
     kern_f = {}
     if full:
@@ -654,6 +666,8 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
         "config": {"workload": desc, "rays_per_step": n,
                    "occupancy": [round(float(sc.occ[l].mean()), 4) for l in range(sc.levels)],
                    "step": "vdb rebuild + hdda walk and emit (stream-ordered) + composite",
+                   "ray_order": f"each camera's pixels row by row, image width {img_w} passed "
+                                "(hdda_params.image_width: the walk takes 8x4 pixel blocks)",
                    "l2": "flushed between steps (256 MiB write), flush outside timed windows",
                    "parallelism": f"replicas x{world}"},
         "samples_per_s": round(samples * world / (ms / 1e3), 1),
@@ -696,6 +710,16 @@ def measure_frame(args, workload: str, full: bool = True) -> dict:
             "speedup_vs_separate": round(ms_sh / ms_fu_s, 3),
             "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(1, v[0]), 4)}
                         for k, v in kern_fu.items()}},
+        "ray_order": {
+            "note": "the same step and samplers without the image width: the walk takes "
+                    "32 consecutive rays (an image-row segment) per warp; same outputs",
+            "step_ms": round(ms_io / K, 4),
+            "hdda_sampler_ms_per_frame": round(ms_io_s / K, 4),
+            "dense_sampler_ms_per_frame": round(ms_io_d / K2, 4),
+            "walk_ms": (round(kern_io["hdda_walk"][1] / max(1, kern_io["hdda_walk"][0]), 4)
+                        if "hdda_walk" in kern_io else None),
+            "hdda_sampler_speedup_of_blocks": round(ms_io_s / ms_sh, 3),
+            "dense_sampler_speedup_of_blocks": round(ms_io_d / ms_sd, 3)},
         "hdda_vs_dense_sampler_speedup": round(ms_sd / K2 / (ms_sh / K), 3),
         "grid": {"vdb_bytes": grid_bytes, "vdb_plain_bytes": plain_bytes,
                  "dense_bytes": int(vstats.dense_bytes),
@@ -881,7 +905,10 @@ def profile_step(args):
     dense = torch.from_numpy(sc.occ).cuda()
     field = torch.from_numpy(sc.field).cuda()
     p = sc.params
-    prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
+    # the rays in image order with the image width, as the bench's timed loops pass them
+    # (a ray prefix of --profile-rays keeps it: whole rows and a partial last one)
+    prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps,
+                           image_width=cams[0].width)
     vdb = args.profile_step in ("hdda", "render")
     hdda.set_sampler_form(hdda.SAMPLER_FUSED if args.sampler_form == "fused"
                           else hdda.SAMPLER_SEPARATE)

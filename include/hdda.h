@@ -79,6 +79,16 @@ typedef struct {
  * 0 <= max_steps <= 2^24.  More candidates than max_steps is
  * HDDA_ERR_STEP_LIMIT.  Directions need not be unit length: t is in units
  * of |d|.
+ *
+ * image_width is a hint on the order of the rays, not a lattice parameter:
+ * 0, or the width W of an image whose pixels the rays are, row by row (ray r
+ * is pixel (r mod W, r div W); the last row may be partial).  With W > 0 the
+ * walk of hdda_traverse_hdda, hdda_traverse_dense, hdda_traverse_async,
+ * hdda_render and hdda_traverse_composite takes the rays in 8 x 4 pixel
+ * blocks, so that the rays a warp walks together are neighbours in both
+ * image axes; every output is the same as with 0, bit for bit.  The fused
+ * sampler form, the batched sampler and hdda_traverse_hdda_noalloc ignore
+ * it.  Negative is HDDA_ERR_INVALID_ARG.
  */
 typedef struct {
     float near_t;
@@ -87,6 +97,7 @@ typedef struct {
     float cone_angle;
     float max_step;
     int32_t max_steps;
+    int32_t image_width;
 } hdda_params;
 
 typedef struct hdda_grid hdda_grid; /* opaque, library-owned device object */

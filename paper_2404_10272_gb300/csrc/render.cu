@@ -260,12 +260,10 @@ const char* render_name(int mode) {
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Scratch: [0, 256) header {walk counter u32, status u32}, then tile sums,
-// counts, run counts and runs.
+// Scratch: [0, 256) header {walk counter u32, status u32}, then counts, run
+// counts and runs (the render kernel needs no tile sums: the walk skips them).
 size_t render_scratch_bytes(int64_t n) {
-  const int64_t T = (n + 31) / 32;
-  return 256 + a256(8 * (size_t)T) + a256(4 * (size_t)n) + a256((size_t)n) +
-         a256(sizeof(uint2) * kMaxRuns * (size_t)n);
+  return 256 + a256(4 * (size_t)n) + a256((size_t)n) + a256(sizeof(uint2) * kMaxRuns * (size_t)n);
 }
 
 // Pinned host word for the synchronous status read.
@@ -276,14 +274,11 @@ struct HostWord {
 thread_local HostWord t_word;
 
 int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
-                  const LatticeDev& lat, const float* field, int G, float* rgba,
+                  const LatticeDev& lat, int32_t width, const float* field, int G, float* rgba,
                   unsigned* dev_status, char* scratch, cudaStream_t s) {
-  const int64_t T = (n + 31) / 32;
   unsigned* counter = reinterpret_cast<unsigned*>(scratch);
   unsigned* status = dev_status ? dev_status : counter + 1;
   char* p = scratch + 256;
-  int64_t* tile_sum = reinterpret_cast<int64_t*>(p);
-  p += a256(8 * (size_t)T);
   int32_t* counts = reinterpret_cast<int32_t*>(p);
   p += a256(4 * (size_t)n);
   uint8_t* nr = reinterpret_cast<uint8_t*>(p);
@@ -291,7 +286,8 @@ int launch_render(const float* ro, const float* rd, int64_t n, const hdda_grid* 
   uint2* runs = reinterpret_cast<uint2*>(p);
   HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
   const int mode = walk_mode(grid);
-  const WalkArgs w{ro, rd, n, grid->view(), lat, counts, nr, runs, tile_sum, counter, status};
+  WalkArgs w{ro, rd, n, grid->view(), lat, counts, nr, runs, nullptr, counter, status};
+  w.width = (int32_t)(width < n ? width : n);
   const size_t stage = stage_layout(lat.K, w.g.L, w.g.R, grid->nodes_total(), mode).bytes;
   {
     KernelTimer kt(walk_name(mode), s);
@@ -343,7 +339,8 @@ const char* sample_composite_name(int mode) {
 // Walk, tile scan, then the storing render kernel: the samplers' outputs and
 // the frame in one pass over the samples.
 int launch_sample_composite(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
-                            const LatticeDev& lat, const float* field, int G, float* rgba,
+                            const LatticeDev& lat, int32_t width, const float* field, int G,
+                            float* rgba,
                             int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
                             int64_t capacity, unsigned* status, char* scratch, cudaStream_t s) {
   const int64_t T = (n + 31) / 32;
@@ -359,9 +356,11 @@ int launch_sample_composite(const float* ro, const float* rd, int64_t n, const h
   uint8_t* nr = reinterpret_cast<uint8_t*>(p);
   p += a256((size_t)n);
   uint2* runs = reinterpret_cast<uint2*>(p);
-  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, s));
+  // a walk in pixel blocks adds the tile sums up atomically: clear them too
+  WalkArgs w{ro, rd, n, grid->view(), lat, counts, nr, runs, tile_sum, counter, status};
+  w.width = (int32_t)(width < n ? width : n);
+  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, w.width > 0 ? 256 + 8 * (size_t)T : 256, s));
   const int mode = walk_mode(grid);
-  const WalkArgs w{ro, rd, n, grid->view(), lat, counts, nr, runs, tile_sum, counter, status};
   const size_t stage = stage_layout(lat.K, w.g.L, w.g.R, grid->nodes_total(), mode).bytes;
   {
     KernelTimer kt(walk_name(mode), s);
@@ -452,8 +451,8 @@ extern "C" int hdda_render(const float* rays_o, const float* rays_d, int64_t n_r
   }
   char* scratch = nullptr;
   HDDA_CUDA_TRY(cudaMallocAsync(&scratch, render_scratch_bytes(n_rays), s));
-  st = launch_render(rays_o, rays_d, n_rays, grid, lat, field, n_gauss, rgba_out, dev_status,
-                     scratch, s);
+  st = launch_render(rays_o, rays_d, n_rays, grid, lat, params->image_width, field, n_gauss,
+                     rgba_out, dev_status, scratch, s);
   if (st == HDDA_OK && !dev_status) {
     cudaError_t e = cudaMemcpyAsync(hw, scratch + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) st = cuda_error(e, "cudaMemcpyAsync(status)");
@@ -507,8 +506,9 @@ extern "C" int hdda_traverse_composite(const float* rays_o, const float* rays_d,
   }
   char* scratch = nullptr;
   HDDA_CUDA_TRY(cudaMallocAsync(&scratch, sample_composite_scratch_bytes(n_rays), s));
-  st = launch_sample_composite(rays_o, rays_d, n_rays, grid, lat, field, n_gauss, rgba_out,
-                               offsets, ray_idx, t0, t1, capacity, dev_status, scratch, s);
+  st = launch_sample_composite(rays_o, rays_d, n_rays, grid, lat, params->image_width, field,
+                               n_gauss, rgba_out, offsets, ray_idx, t0, t1, capacity, dev_status,
+                               scratch, s);
   cudaError_t e = cudaFreeAsync(scratch, s);
   if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
   return st;

@@ -49,6 +49,7 @@
 // kernel, onepass_kernel, whose CTAs keep the runs in shared memory and look
 // back right after walking, so its scratch stays a few hundred kilobytes.  A
 // ray with more runs than are kept walks again and writes its own samples.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -674,6 +675,8 @@ int validate_params(const hdda_params* p) {
     return set_error(HDDA_ERR_INVALID_ARG, "need step > 0, max_step > 0, cone_angle >= 0");
   if (p->max_steps < 0 || p->max_steps > (1 << 24))
     return set_error(HDDA_ERR_INVALID_ARG, "max_steps=%d outside 0..2^24", p->max_steps);
+  if (p->image_width < 0)
+    return set_error(HDDA_ERR_INVALID_ARG, "image_width=%d < 0", p->image_width);
   return HDDA_OK;
 }
 
@@ -836,9 +839,9 @@ const char* emit_name(int mode) {
 // both passes in one kernel (walk_emit_kernel), whose look-back states take
 // the tile sums' space.
 int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* grid,
-                const LatticeDev& lat, int64_t* offsets, int32_t* ray_idx, float* t0, float* t1,
-                int64_t capacity, int64_t* total_out, char* scratch, int64_t* hw,
-                unsigned* dev_status, cudaStream_t s) {
+                const LatticeDev& lat, int32_t width, int64_t* offsets, int32_t* ray_idx,
+                float* t0, float* t1, int64_t capacity, int64_t* total_out, char* scratch,
+                int64_t* hw, unsigned* dev_status, cudaStream_t s) {
   const int64_t T = (n + 31) / 32;
   unsigned* walk_counter = reinterpret_cast<unsigned*>(scratch);
   unsigned* status = dev_status ? dev_status : walk_counter + 1;
@@ -885,7 +888,14 @@ int run_twopass(const float* ro, const float* rd, int64_t n, const hdda_grid* gr
     if (dev_status) return HDDA_OK;  // stream-ordered: nothing is read back
     return finish(hw, scratch, capacity, total_out, s);
   }
-  HDDA_CUDA_TRY(cudaMemsetAsync(scratch, 0, kTwopassHead + 8 * (size_t)(G32 + G1024), s));
+  // a walk in pixel blocks adds the tile sums up atomically: region B is
+  // cleared too (it follows region A)
+  w.width = (int32_t)std::min<int64_t>(width, n);
+  HDDA_CUDA_TRY(cudaMemsetAsync(
+      scratch, 0,
+      w.width > 0 ? kTwopassHead + a256(8 * (size_t)T) + 8 * (size_t)T
+                  : kTwopassHead + 8 * (size_t)(G32 + G1024),
+      s));
   w.sums32 = sums32;
   w.sums1024 = sums1024;
   {
@@ -940,8 +950,8 @@ int traverse(bool vdb, const float* ro, const float* rd, int64_t n, const hdda_g
   if (st != HDDA_OK) return st;
   char* scratch = nullptr;
   HDDA_CUDA_TRY(cudaMallocAsync(&scratch, twopass_scratch_bytes(n), s));
-  st = run_twopass(ro, rd, n, grid, lat, offsets, ray_idx, t0, t1, capacity, total_out, scratch,
-                   hw, nullptr, s);
+  st = run_twopass(ro, rd, n, grid, lat, params->image_width, offsets, ray_idx, t0, t1, capacity,
+                   total_out, scratch, hw, nullptr, s);
   cudaError_t e = cudaFreeAsync(scratch, s);
   if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
   return st;
@@ -970,8 +980,8 @@ int traverse_async(const float* ro, const float* rd, int64_t n, const hdda_grid*
   }
   char* scratch = nullptr;
   HDDA_CUDA_TRY(cudaMallocAsync(&scratch, twopass_scratch_bytes(n), s));
-  st = run_twopass(ro, rd, n, grid, lat, offsets, ray_idx, t0, t1, capacity, &unused_total,
-                   scratch, nullptr, dev_status, s);
+  st = run_twopass(ro, rd, n, grid, lat, params->image_width, offsets, ray_idx, t0, t1,
+                   capacity, &unused_total, scratch, nullptr, dev_status, s);
   cudaError_t e = cudaFreeAsync(scratch, s);
   if (st == HDDA_OK && e != cudaSuccess) st = cuda_error(e, "cudaFreeAsync");
   return st;

@@ -783,17 +783,33 @@ __device__ __forceinline__ void stage_walk_tables(unsigned char* smem, const Gri
   }
 }
 
-// Pass 1.  Persistent: each warp takes 32-ray tiles in order until none is
-// left, so a warp never waits for another.  Writes counts[r], nruns[r]
-// (saturated at 255), the first kMaxRuns runs at runs[r + j * n] and each
-// tile's sample total at tile_sum[tile].
+// Adds v samples to 32-ray tile t: its sum and, when kept, the sums of its
+// groups of 32 and of 1024 tiles (all zeroed by the caller).
+__device__ __forceinline__ void add_tile_sum(int64_t t, int64_t v, int64_t* tile_sum,
+                                             unsigned long long* sums32,
+                                             unsigned long long* sums1024) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(tile_sum) + t, (unsigned long long)v);
+  if (sums32) {
+    atomicAdd(sums32 + (t >> 5), (unsigned long long)v);
+    atomicAdd(sums1024 + (t >> 10), (unsigned long long)v);
+  }
+}
+
+// Pass 1.  Persistent: each warp takes work tiles in order until none is
+// left, so a warp never waits for another.  A work tile is 32 consecutive
+// rays, or, when the rays are the pixels of a `width`-wide image row by row
+// (width > 0), a block of 8 x 4 pixels, whose rays start and end their
+// regions at more similar depths.  Writes counts[r], nruns[r] (saturated at
+// 255) and the first kMaxRuns runs at runs[r + j * n], and, unless tile_sum
+// is null, each 32-ray tile's sample total at tile_sum[r / 32]: stored in
+// index order, added atomically in block order (then zeroed by the caller).
 template <int kMode, bool kSm, bool kSkip, bool kCheck>
 __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     const float* __restrict__ ro, const float* __restrict__ rd, int64_t n, GridDev g,
     LatticeDev lat, int32_t* __restrict__ counts, uint8_t* __restrict__ nruns_out,
     uint2* __restrict__ runs, int64_t* __restrict__ tile_sum, unsigned* __restrict__ tile_counter,
     unsigned* __restrict__ status, unsigned long long* __restrict__ sums32,
-    unsigned long long* __restrict__ sums1024) {
+    unsigned long long* __restrict__ sums1024, int32_t width) {
   extern __shared__ __align__(16) unsigned char smem[];
   const LatHdr h = lat_hdr(lat);
   Tabs tb = global_tabs(g);
@@ -802,16 +818,35 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
     stage_walk_tables<kMode>(smem, g, lat, h, tb, ls);
     __syncthreads();
   }
+  // work tiles, and block columns: 8 x 4 blocks over ceil(n / width) rows.
+  // Kept in shared memory, not in registers across the walk.
+  __shared__ unsigned s_tiles[2];
+  if (threadIdx.x == 0) {
+    const unsigned bc = width > 0 ? ((unsigned)width + 7) / 8 : 0;
+    s_tiles[0] = width > 0 ? bc * (unsigned)(((n + width - 1) / width + 3) / 4)
+                           : (unsigned)((n + 31) / 32);
+    s_tiles[1] = bc;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
-  const unsigned ntiles = (unsigned)((n + 31) / 32);
   for (;;) {
     unsigned tile = 0;
     if (lane == 0) tile = atomicAdd(tile_counter, 1u);
     tile = __shfl_sync(kFull, tile, 0);
-    if (tile >= ntiles) break;
-    const int64_t r = (int64_t)tile * 32 + lane;
+    if (tile >= s_tiles[0]) break;
+    int64_t r;
+    bool ok;
+    if (width > 0) {
+      const unsigned bcols = s_tiles[1];
+      const unsigned by = tile / bcols, x = (tile - by * bcols) * 8 + (lane & 7);
+      r = (int64_t)(by * 4 + (lane >> 3)) * width + x;
+      ok = x < (unsigned)width && r < n;
+    } else {
+      r = (int64_t)tile * 32 + lane;
+      ok = r < n;
+    }
     int64_t c = 0;
-    if (r < n) {
+    if (ok) {
       Ray ray;
       int nr = 0;
       if (load_ray(ro, rd, r, ray))
@@ -820,13 +855,32 @@ __global__ void __launch_bounds__(kWalkBS) walk_kernel(
       counts[r] = (int32_t)c;
       nruns_out[r] = (uint8_t)min(nr, 255);
     }
+    if (!tile_sum) continue;
+    if (width > 0) {
+      // the 8 lanes of a block row hold consecutive rays, so at most two
+      // 32-ray tiles: the row leader's and the next.  A row whose leader is
+      // out of range has no ray in range.
+      const int64_t t = r >> 5, ta = __shfl_sync(kFull, t, lane & ~7);
+      int64_t a = t == ta ? c : 0, b = c - a;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(kFull, a, o);
+        b += __shfl_xor_sync(kFull, b, o);
+      }
+      if ((lane & 7) == 0) {
+        if (a) add_tile_sum(ta, a, tile_sum, sums32, sums1024);
+        if (b) add_tile_sum(ta + 1, b, tile_sum, sums32, sums1024);
+      }
+      continue;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
     if (lane == 0) {
-      tile_sum[tile] = c;
+      const int64_t t = r >> 5;  // lane 0's ray opens the tile
+      tile_sum[t] = c;
       if (sums32) {  // the group sums tile_offset reads (zeroed by the caller)
-        atomicAdd(sums32 + (tile >> 5), (unsigned long long)c);
-        atomicAdd(sums1024 + (tile >> 10), (unsigned long long)c);
+        atomicAdd(sums32 + (t >> 5), (unsigned long long)c);
+        atomicAdd(sums1024 + (t >> 10), (unsigned long long)c);
       }
     }
   }
@@ -877,6 +931,7 @@ struct WalkArgs {
   unsigned* status;
   unsigned long long* sums32 = nullptr;    // optional group sums for tile_offset
   unsigned long long* sums1024 = nullptr;
+  int32_t width = 0;                       // image width: walk in 8 x 4 pixel blocks
 };
 
 template <int kMode, bool kSm, bool kSkip>
@@ -899,7 +954,8 @@ int launch_walk(const WalkArgs& w, size_t smem, cudaStream_t s) {
   const int64_t full = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
   const unsigned grid = (unsigned)(want < full ? want : full);
   kern<<<grid, kWalkBS, smem, s>>>(w.ro, w.rd, w.n, w.g, w.lat, w.counts, w.nruns, w.runs,
-                                   w.tile_sum, w.counter, w.status, w.sums32, w.sums1024);
+                                   w.tile_sum, w.counter, w.status, w.sums32, w.sums1024,
+                                   w.width);
   HDDA_CUDA_TRY(cudaGetLastError());
   return HDDA_OK;
 }

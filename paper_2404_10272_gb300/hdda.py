@@ -50,7 +50,7 @@ class AABB(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("near_t", ctypes.c_float), ("far_t", ctypes.c_float), ("step", ctypes.c_float),
                 ("cone_angle", ctypes.c_float), ("max_step", ctypes.c_float),
-                ("max_steps", ctypes.c_int32)]
+                ("max_steps", ctypes.c_int32), ("image_width", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -180,8 +180,9 @@ def _aabbs(aabbs, levels):
     return arr
 
 
-def make_params(near, far, step, cone=0.0, max_step=1e10, max_steps=1 << 20) -> Params:
-    return Params(near, far, step, cone, max_step, max_steps)
+def make_params(near, far, step, cone=0.0, max_step=1e10, max_steps=1 << 20,
+                image_width=0) -> Params:
+    return Params(near, far, step, cone, max_step, max_steps, image_width)
 
 
 class Grid:
