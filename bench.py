@@ -54,9 +54,11 @@ KERNELS_PER_TIMER = {"build_vdb": 5}   # the builder's timer spans five kernels
 # from the ncu --set full captures (object frame, camera 0; unbounded: its first 200 image
 # rows); dropped like the traffic when a kernel changes.
 PROFILED_COUNTERS = {
-    "object": {"hdda_emit": {"l2_hit_pct": 10.7, "active_lanes_of_32": 27.16},
+    "object": {"hdda_walk": {"l2_hit_pct": 53.8, "active_lanes_of_32": 26.06},
+               "hdda_emit": {"l2_hit_pct": 10.7, "active_lanes_of_32": 27.16},
                "composite": {"l2_hit_pct": 26.4, "active_lanes_of_32": 30.03}},
-    "unbounded": {"hdda_emit": {"l2_hit_pct": 10.0, "active_lanes_of_32": 30.15},
+    "unbounded": {"hdda_walk": {"l2_hit_pct": 56.7, "active_lanes_of_32": 26.01},
+                  "hdda_emit": {"l2_hit_pct": 10.0, "active_lanes_of_32": 30.15},
                   "composite": {"l2_hit_pct": 16.6, "active_lanes_of_32": 30.46}},
 }
 # DRAM bytes (read + write) per launch from ncu of a workload's step on camera 0 (the
@@ -64,8 +66,9 @@ PROFILED_COUNTERS = {
 # entry must be dropped whenever its kernel changes, and a workload without a capture
 # reports none.
 PROFILED_TRAFFIC = {
-    "object": {"composite": 233_765_120, "hdda_emit": 266_570_240},
-    "unbounded": {"composite": 1_502_329_856, "hdda_emit": 2_182_360_576},
+    "object": {"composite": 233_599_744, "hdda_emit": 266_574_592, "hdda_walk": 16_295_424},
+    "unbounded": {"composite": 1_502_165_760, "hdda_emit": 2_182_214_144,
+                  "hdda_walk": 27_365_888},
 }
 
 
@@ -1056,15 +1059,16 @@ def run_serve(args, quick: bool = False) -> dict:
         W = int(round(math.exp(rng.uniform(math.log(200), math.log(1920)))))
         H = int(round(math.exp(rng.uniform(math.log(200), math.log(1080)))))
         o, d = scenes.orbit_camera(rng, 4.0, W, H, 0.69).rays()
-        pool.append((torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory()))
+        pool.append((torch.from_numpy(o).pin_memory(), torch.from_numpy(d).pin_memory(), W))
     slots = 4
     budget = 8 << 30
     seconds = 2.5 if quick else 6.0
     pick = random.Random(7)
 
     def make(rid):
-        o, d = pool[pick.randrange(len(pool))]
-        return serve.Request(rid=rid, scene=pick.randrange(len(scene_list)), rays_o=o, rays_d=d)
+        o, d, w = pool[pick.randrange(len(pool))]
+        return serve.Request(rid=rid, scene=pick.randrange(len(scene_list)), rays_o=o, rays_d=d,
+                             width=w)
 
     def capacity(ex):
         srv = serve.RenderServer(ex, slots=slots, budget_bytes=budget)

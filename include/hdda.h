@@ -360,8 +360,8 @@ int hdda_traverse_async(const float* rays_o, const float* rays_d, int64_t n_rays
  * (cudaGetSymbolAddress) and should come before any stream capture.  All
  * calls share the array: calls whose GPU work overlaps race on it and must
  * be serialised by the caller.  Every call, not only the first, synchronises
- * the stream twice (lattice length, sample total); every output is complete
- * when it returns.
+ * the stream twice (lattice length, sample total), so no call can be
+ * captured into a CUDA graph; every output is complete when it returns.
  */
 int hdda_traverse_hdda_noalloc(const float* rays_o, const float* rays_d, int64_t n_rays,
                                const hdda_grid* grid, const hdda_params* params,

@@ -68,6 +68,7 @@ class Request:
     retries: int = 0
     rgba: object = None        # host float32 [n, 4]
     error: str | None = None
+    width: int = 0             # image width when the rays are an image's pixels row by row
 
     @property
     def n_rays(self) -> int:
@@ -277,6 +278,15 @@ class GpuExecutor:
         self.status_host = [torch.zeros(1, dtype=torch.int32, pin_memory=True)
                             for _ in range(slots)]
 
+    def _params(self, req: Request):
+        """The scene's parameters, with the request's image width as the ray-order hint."""
+        base = self.params[req.scene]
+        if req.width <= 0:
+            return base
+        prm = type(base).from_buffer_copy(base)
+        prm.image_width = req.width
+        return prm
+
     def warm(self) -> None:
         """First use of each scene's lattice synchronises; do it before serving."""
         torch, hdda = self.torch, self.hdda
@@ -295,7 +305,7 @@ class GpuExecutor:
             o = req.rays_o.to("cuda", non_blocking=True)
             d = req.rays_d.to("cuda", non_blocking=True)
             out = hdda.alloc_samples(n, cap)
-            g, prm, fld = self.grids[req.scene], self.params[req.scene], self.fields[req.scene]
+            g, prm, fld = self.grids[req.scene], self._params(req), self.fields[req.scene]
             try:
                 smp = hdda.traverse_hdda(o, d, g, prm, out=out, stream=s)
             except hdda.HddaError as e:
@@ -357,7 +367,7 @@ class GpuExecutor:
             o = req.rays_o.to("cuda", non_blocking=True)
             d = req.rays_d.to("cuda", non_blocking=True)
             st.zero_()
-            g, prm, fld = self.grids[req.scene], self.params[req.scene], self.fields[req.scene]
+            g, prm, fld = self.grids[req.scene], self._params(req), self.fields[req.scene]
             rgba = hdda.render(o, d, g, prm, fld, status=st, stream=s)
             host = torch.empty((n, 4), dtype=torch.float32, pin_memory=True)
             host.copy_(rgba, non_blocking=True)

@@ -31,7 +31,7 @@ def _rays(seed, W, H):
 def test_alone_equals_mixed_and_direct(setup):
     hdda, sc, ex = setup
     o, d = _rays(1, 320, 240)
-    alone = serve.Request(rid=0, scene=1, rays_o=o, rays_d=d)
+    alone = serve.Request(rid=0, scene=1, rays_o=o, rays_d=d, width=320)
     srv = serve.RenderServer(ex, slots=4, budget_bytes=4 << 30)
     srv.submit(alone)
     srv.close()
@@ -40,8 +40,9 @@ def test_alone_equals_mixed_and_direct(setup):
     mix = []
     for i in range(12):
         oo, dd = _rays(100 + i, 64 + 40 * i, 48 + 30 * i)
-        mix.append(serve.Request(rid=i + 1, scene=i % 2, rays_o=oo, rays_d=dd))
-    target = serve.Request(rid=99, scene=1, rays_o=o, rays_d=d)
+        mix.append(serve.Request(rid=i + 1, scene=i % 2, rays_o=oo, rays_d=dd,
+                                 width=64 + 40 * i))
+    target = serve.Request(rid=99, scene=1, rays_o=o, rays_d=d, width=320)
     for r in mix[:6] + [target] + mix[6:]:
         srv.submit(r)
     srv.close()
@@ -52,7 +53,7 @@ def test_alone_equals_mixed_and_direct(setup):
     assert diff <= TOL
     # the low hint forces re-runs at the exact size somewhere in the mix
     assert sum(r.retries for r in mix + [target]) > 0
-    # direct API
+    # direct API, with the rays in index order (the server passed the image width)
     p = sc[1].params
     prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
     s = hdda.traverse_hdda(o.cuda(), d.cuda(), ex.grids[1], prm)
@@ -66,7 +67,7 @@ def test_render_mode_alone_equals_mixed_and_direct(setup):
     ex = serve.GpuExecutor(sc, slots=4, mode="render")
     ex.warm()
     o, d = _rays(2, 320, 240)
-    alone = serve.Request(rid=0, scene=1, rays_o=o, rays_d=d)
+    alone = serve.Request(rid=0, scene=1, rays_o=o, rays_d=d, width=320)
     srv = serve.RenderServer(ex, slots=4, budget_bytes=1 << 30)
     srv.submit(alone)
     srv.close()
@@ -75,15 +76,17 @@ def test_render_mode_alone_equals_mixed_and_direct(setup):
     mix = []
     for i in range(12):
         oo, dd = _rays(200 + i, 64 + 40 * i, 48 + 30 * i)
-        mix.append(serve.Request(rid=i + 1, scene=i % 2, rays_o=oo, rays_d=dd))
-    target = serve.Request(rid=99, scene=1, rays_o=o, rays_d=d)
+        mix.append(serve.Request(rid=i + 1, scene=i % 2, rays_o=oo, rays_d=dd,
+                                 width=64 + 40 * i))
+    target = serve.Request(rid=99, scene=1, rays_o=o, rays_d=d, width=320)
     for r in mix[:6] + [target] + mix[6:]:
         srv.submit(r)
     srv.close()
     assert all(r.error is None and r.retries == 0 for r in mix + [target])
     assert srv.max_concurrent > 1
     assert torch.equal(target.rgba, alone.rgba)
-    # direct API, and the sample-buffer path within the compositor's tolerance
+    # direct API with the rays in index order (bit for bit: the server passed the image
+    # width), and the sample-buffer path within the compositor's tolerance
     p = sc[1].params
     prm = hdda.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps)
     direct = hdda.render(o.cuda(), d.cuda(), ex.grids[1], prm, ex.fields[1]).cpu()
