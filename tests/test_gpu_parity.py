@@ -202,9 +202,13 @@ def test_tiny_scene_full_frame(H):
     assert ref[0][-1] > 0
 
 
-def _full_vs_subset(H, sc, o, d, stride, what):
+def _full_vs_subset(H, sc, o, d, width, stride, what):
     gd, gv = both_grids(H, sc.occ, sc.aabbs)
     prm = P(H, sc.params)
+    p = sc.params
+    # the launch the benchmark times: the image width passed (8 x 4 pixel blocks)
+    prm_w = H.make_params(p.near, p.far, p.step, p.cone, p.max_step, p.max_steps,
+                          image_width=width)
     ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
     dense = gpu_samples(H, "dense", ot, dt, gd, prm)
     vdb = gpu_samples(H, "hdda", ot, dt, gv, prm)
@@ -212,22 +216,26 @@ def _full_vs_subset(H, sc, o, d, stride, what):
     gv.set_refine(False)
     assert_same(gpu_samples(H, "hdda", ot, dt, gv, prm), vdb, what + " full frame: plain vs refined")
     gv.set_refine(True)
-    # the library default (region checks off), as the benchmark runs it
+    # the library default (region checks off) and the image width, as the benchmark runs it
     H.set_region_checks(False)
     try:
         assert_same(gpu_samples(H, "hdda", ot, dt, gv, prm), vdb, what + " full frame: checks off")
         assert_same(gpu_samples(H, "dense", ot, dt, gd, prm), dense,
                     what + " full frame: dense, checks off")
+        timed = gpu_samples(H, "hdda", ot, dt, gv, prm_w)
+        assert_same(timed, vdb, what + " full frame: pixel blocks, checks off")
+        assert_same(gpu_samples(H, "dense", ot, dt, gd, prm_w), dense,
+                    what + " full frame: dense, pixel blocks, checks off")
     finally:
         H.set_region_checks(True)
     with sampler_form(H, H.SAMPLER_FUSED):
         assert_same(gpu_samples(H, "hdda", ot, dt, gv, prm), vdb, what + " full frame: fused")
         assert_same(gpu_samples(H, "dense", ot, dt, gd, prm), dense,
                     what + " full frame: dense, fused")
-    # oracle on a stratified subset of the same launch's rays
+    # oracle on a stratified subset of the timed launch's rays
     so, sd, sel = subset_rays(o, d, stride, offset=stride // 3)
     ref = oracle_samples(so, sd, sc.occ, sc.aabbs, sc.params)
-    off, idx, t0, t1 = vdb
+    off, idx, t0, t1 = timed
     for j, r in enumerate(sel):
         a, b = off[r], off[r + 1]
         ra, rb = ref[0][j], ref[0][j + 1]
@@ -241,14 +249,14 @@ def _full_vs_subset(H, sc, o, d, stride, what):
 def test_object_scene_full_size(H):
     sc = scenes.object_scene()
     o, d = scenes.object_cameras(n=1)[0].rays()
-    vdb = _full_vs_subset(H, sc, o, d, 97, "object 800x800")
+    vdb = _full_vs_subset(H, sc, o, d, 800, 97, "object 800x800")
     assert vdb[0][-1] > 1_000_000
 
 
 def test_unbounded_scene_full_size(H):
     sc = scenes.unbounded_scene()
     o, d = scenes.unbounded_camera().rays()
-    vdb = _full_vs_subset(H, sc, o, d, 211, "unbounded 1245x825")
+    vdb = _full_vs_subset(H, sc, o, d, 1245, 211, "unbounded 1245x825")
     assert vdb[0][-1] > 0
 
 
